@@ -1,0 +1,65 @@
+"""The seeded generator draws balanced, covered, reproducible networks."""
+import numpy as np
+import pytest
+
+from paper_2511_10558_gb300 import synth
+
+
+@pytest.mark.parametrize("S,R", [(32, 200), (150, 1500)])
+def test_balanced_and_covered(S, R):
+    net = synth.make_network(S, R)
+    assert net.n_species == S and net.n_reactions == R
+    key = np.hstack([net.composition, net.charge[:, None]])
+    sigs = set()
+    for j in range(R):
+        rc = [a for a in net.reac[j] if a >= 0]
+        pr = [p for p in net.prod[j] if p >= 0]
+        assert 1 <= len(rc) <= 2 and 1 <= len(pr) <= 4
+        assert (net.rtype[j] == synth.TWO_BODY) == (len(rc) == 2)
+        np.testing.assert_array_equal(key[rc].sum(0), key[pr].sum(0))
+        assert sorted(rc) != sorted(pr)
+        sig = (int(net.rtype[j]), tuple(sorted(rc)), tuple(sorted(pr)))
+        assert sig not in sigs
+        sigs.add(sig)
+    reactant = np.zeros(S, bool)
+    product = np.zeros(S, bool)
+    for j in range(R):
+        reactant[[a for a in net.reac[j] if a >= 0]] = True
+        product[[p for p in net.prod[j] if p >= 0]] = True
+    assert reactant.all() and product.all()
+    counts = np.bincount(net.rtype, minlength=3)
+    assert counts[0] == round(0.7 * R) and counts[1] == round(0.15 * R)
+    # species are unique (composition, charge) pairs and the electron is species 0
+    assert len({tuple(k) for k in key}) == S
+    assert net.names[0] == "e-" and net.charge[0] == -1 and key[0, :5].sum() == 0
+
+
+def test_parameter_ranges(net150):
+    tb = net150.rtype == synth.TWO_BODY
+    cr = net150.rtype == synth.COSMIC_RAY
+    ph = net150.rtype == synth.PHOTO
+    assert np.all((net150.alpha[tb] >= 1e-12) & (net150.alpha[tb] <= 1e-9))
+    assert np.all(np.abs(net150.beta[tb]) <= 1)
+    assert np.all((net150.gamma[tb] >= 0) & (net150.gamma[tb] <= 500))
+    assert 0.35 < np.mean(net150.gamma[tb] == 0) < 0.65
+    assert np.all((net150.alpha[cr] >= 1) & (net150.alpha[cr] <= 1e3))
+    assert np.all((net150.alpha[ph] >= 1e-11) & (net150.alpha[ph] <= 1e-9))
+    assert np.all((net150.gamma[ph] >= 1) & (net150.gamma[ph] <= 3))
+
+
+def test_reproducible():
+    a = synth.make_network(32, 200)
+    b = synth.make_network(32, 200)
+    np.testing.assert_array_equal(a.reac, b.reac)
+    np.testing.assert_array_equal(a.alpha, b.alpha)
+    c = synth.cells(64)
+    assert np.all((c[:, 0] >= 1e2) & (c[:, 0] <= 1e6))
+    assert np.all((c[:, 1] >= 10) & (c[:, 1] <= 300))
+    assert np.all((c[:, 2] >= 0) & (c[:, 2] <= 20))
+    np.testing.assert_array_equal(c, synth.cells(64))
+
+
+def test_initial_abundances(net32):
+    x = synth.initial_abundances(net32)
+    assert x[net32.index("H2")] == 0.5 and x[net32.index("e-")] == x[net32.index("C+")]
+    assert np.sum(x == 1e-20) == net32.n_species - 6
