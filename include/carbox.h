@@ -1,0 +1,194 @@
+/*
+ * carbox.h - C ABI of the GB300 batched astrochemistry solver.
+ *
+ * The library integrates many independent zero-dimensional gas cells through
+ * one mass-action chemical reaction network. The method is the one of the
+ * paper "Carbox: an end-to-end differentiable astrochemical simulation
+ * framework" (arXiv 2511.10558):
+ *
+ *   - the network: species and reactions in a uniform format, from which the
+ *     incidence (stoichiometry) matrix is built (Sec. 4);
+ *   - the ODE  dn_i/dt = +-sum_j k_j n_s1 +- sum_j k_j n_s1 n_s2 (Sec. 2), with
+ *     rate coefficients k(phi) of the environment phi = (T, zeta, F_UV, ...)
+ *     (Sec. 2: n' = f(n, k(phi), phi));
+ *   - rate forms: two-body Kooij-Arrhenius k = alpha (T/300)^beta exp(-gamma/T)
+ *     and direct cosmic-ray ionisation k = alpha zeta (Sec. 2); photo-reactions
+ *     k = alpha F_UV exp(-gamma A_V) (App. B.1);
+ *   - a stiff implicit integrator: variable-order BDF (Sec. 1) with a Newton
+ *     iteration on (I - h gamma J) dx = r, J the analytic sparse Jacobian
+ *     (Sec. 4 names the sparse/dense trade-off).
+ *
+ * State and units. The solver integrates x_i = n_i / n_H (abundance per
+ * hydrogen nucleus) with n_H constant per cell; two-body coefficients are
+ * multiplied by n_H internally. Time is in seconds.
+ *
+ * Conventions for every function:
+ *   - return 0 (CBX_OK) on success, a negative CBX_E* code on error; the
+ *     message of the last error on the calling thread is cbx_last_error();
+ *   - "device pointer" means memory of the current CUDA device (cudaMalloc,
+ *     torch.cuda tensors' data_ptr()); "host pointer" means ordinary memory;
+ *   - the caller owns every array it passes; the library owns networks and
+ *     its internal workspace;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Device-pointer calls are asynchronous on that stream; errors
+ *     found by the host are returned at once, errors of the kernel itself
+ *     surface through later CUDA calls as usual.
+ *   - arrays of per-cell species values are laid out [S][C], cell index
+ *     fastest (x[i*C + c]), species in the order given to cbx_network_create.
+ */
+#ifndef CARBOX_H
+#define CARBOX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CBX_VERSION 1
+
+/* error codes (return values) */
+#define CBX_OK 0
+#define CBX_E_ARG (-1)      /* invalid argument */
+#define CBX_E_CUDA (-2)     /* a CUDA call failed; message has the CUDA error */
+#define CBX_E_NOMEM (-3)    /* host or device allocation failed */
+#define CBX_E_TOO_LARGE (-4) /* network too large for the selected solver */
+
+/* per-cell status codes (cell_status output) */
+#define CBX_CELL_OK 0           /* reached t_end */
+#define CBX_CELL_MAX_STEPS 1    /* max_steps step attempts used */
+#define CBX_CELL_H_UNDERFLOW 2  /* step size fell below 10 ulp(t) */
+#define CBX_CELL_BAD_INPUT 5    /* non-finite or non-physical cell parameters */
+
+/* reaction types (Sec. 2 and App. B.1) */
+#define CBX_TWO_BODY 0    /* A + B -> products, k = alpha (T/300)^beta exp(-gamma/T) */
+#define CBX_COSMIC_RAY 1  /* X -> products,     k = alpha zeta                       */
+#define CBX_PHOTO 2       /* X -> products,     k = alpha G0 exp(-gamma A_V)         */
+
+/* precision of the Newton linear algebra */
+#define CBX_FP64 0   /* LU, triangular solves and everything else in FP64 */
+#define CBX_MIXED 1  /* LU and triangular solves in FP32, FP64 residual r - M dx
+                        against the FP64 matrix and iterative refinement; rates,
+                        right-hand side, error control and the update stay FP64 */
+
+typedef struct {
+  int composition[5]; /* atoms of H, He, C, N, O (used for conservation checks only) */
+  int charge;         /* -1, 0, +1 ... */
+} cbx_species;
+
+typedef struct {
+  int type;     /* CBX_TWO_BODY, CBX_COSMIC_RAY or CBX_PHOTO */
+  int reac[2];  /* reactant species indices; reac[1] = -1 for one-reactant types;
+                   reac[0] == reac[1] is A + A (rate kappa x_A^2, A consumed twice) */
+  int prod[4];  /* product species indices, -1 = absent; at least one product */
+  double alpha, beta, gamma; /* rate parameters of the type's formula */
+} cbx_reaction;
+
+typedef struct {
+  double n_H;   /* hydrogen nucleus density, cm^-3 (> 0) */
+  double T;     /* gas temperature, K (> 0) */
+  double A_V;   /* visual extinction, mag */
+  double G0;    /* UV field F_UV, Habing units */
+  double zeta;  /* cosmic-ray ionisation rate per H2, s^-1 */
+} cbx_cell_params;
+
+typedef struct {
+  double rtol;        /* relative tolerance (> 0) */
+  double atol;        /* absolute tolerance on x (>= 0; rtol*|x| + atol > 0 required) */
+  int max_steps;      /* step attempts per cell before CBX_CELL_MAX_STEPS (> 0) */
+  int precision;      /* CBX_FP64 or CBX_MIXED */
+  int max_refine;     /* CBX_MIXED: refinement sweeps per solve (>= 1) */
+  int reserved;
+  double refine_tol;  /* CBX_MIXED: stop refining when the weighted RMS of the
+                         correction is <= refine_tol */
+} cbx_options;
+
+typedef struct {
+  int steps;          /* accepted steps */
+  int attempts;       /* step attempts (accepted + rejected) */
+  int error_fails;    /* rejected by the local error test */
+  int newton_fails;   /* rejected because Newton did not converge */
+  int rhs_evals;      /* right-hand side evaluations */
+  int jac_evals;      /* Jacobian evaluations */
+  int lu_factors;     /* LU factorisations of I - cJ */
+  int newton_iters;   /* Newton iterations */
+  int refine_sweeps;  /* refinement sweeps (CBX_MIXED) */
+  int reserved;
+} cbx_cell_stats;
+
+typedef struct {
+  int S, R;           /* species, reactions */
+  int nnz_jac;        /* structural non-zeros of J + I */
+  int nnz_lu;         /* non-zeros of the symbolic L + U fill (after ordering) */
+  double lu_flops;    /* flops of one numeric LU on that fill */
+  double lu_flops_dense; /* 2 S^3 / 3 */
+  int smem_bytes_fp64;   /* shared memory per CTA of the FP64 solver */
+  int smem_bytes_mixed;  /* shared memory per CTA of the mixed solver */
+} cbx_netinfo;
+
+typedef struct cbx_network cbx_network;
+
+/* Version of this ABI (CBX_VERSION). */
+int cbx_version(void);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* cbx_last_error(void);
+
+/*
+ * Build a network: the incidence matrix (Sec. 4), the analytic Jacobian's
+ * sparsity pattern, a fill-reducing ordering (minimum degree on the pattern of
+ * J + J^T), the symbolic LU fill of I - cJ in that order, and the gather tables
+ * of the right-hand side and the Jacobian; then upload them to the current
+ * device. Host work, once per network.
+ *   species [S], reactions [R]: host pointers, read only during the call.
+ *   out: receives a library-owned handle (free with cbx_network_destroy).
+ * Errors: CBX_E_ARG for S < 1, R < 0, a bad type, an index out of range, a
+ * one-reactant type with two reactants (or the reverse), or no product;
+ * CBX_E_CUDA / CBX_E_NOMEM for upload failures.
+ */
+int cbx_network_create(const cbx_species* species, int S, const cbx_reaction* reactions, int R,
+                       cbx_network** out);
+
+/* Free a network (NULL is allowed). The caller makes sure no solve using it is in flight. */
+int cbx_network_destroy(cbx_network* net);
+
+/* Sizes and symbolic-analysis figures of a network. */
+int cbx_network_info(const cbx_network* net, cbx_netinfo* out);
+
+/* Default options: rtol 1e-4, atol 1e-20, max_steps 100000, CBX_FP64,
+   max_refine 5, refine_tol 1e-10. */
+int cbx_default_options(cbx_options* out);
+
+/*
+ * Integrate C cells from t0 to t_end (seconds) with the variable-order BDF.
+ *   phi    [C]     device pointer, cell parameters (Sec. 2: k(phi)).
+ *   x0     [S][C]  device pointer, initial abundances per n_H.
+ *   opt            host pointer (NULL = defaults).
+ *   x_out  [S][C]  device pointer, x(t_end) per n_H (may alias nothing else).
+ *   cell_status [C] device pointer, CBX_CELL_* per cell.
+ *   stats  [C]     device pointer or NULL, per-cell counters.
+ * A failing cell never stops the others: it ends with its status and its last
+ * accepted state in x_out. Results of a cell do not depend on C, on the other
+ * cells, or on the launch configuration (bitwise).
+ * Errors: CBX_E_ARG (C < 0, NULL arrays with C > 0, t_end < t0, bad options),
+ * CBX_E_TOO_LARGE (the cell's matrix does not fit the solver), CBX_E_CUDA.
+ */
+int cbx_solve(cbx_network* net, const cbx_cell_params* phi, const double* x0, int C, double t0,
+              double t_end, const cbx_options* opt, void* stream, double* x_out, int* cell_status,
+              cbx_cell_stats* stats);
+
+/*
+ * As cbx_solve, with HOST pointers for phi, x0, x_out, cell_status and stats:
+ * the call copies the inputs to the device, solves, copies the results back
+ * and synchronises `stream` before returning.
+ */
+int cbx_solve_host(cbx_network* net, const cbx_cell_params* phi, const double* x0, int C, double t0,
+                   double t_end, const cbx_options* opt, void* stream, double* x_out,
+                   int* cell_status, cbx_cell_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CARBOX_H */

@@ -1,0 +1,187 @@
+"""ctypes binding of the C ABI in include/carbox.h (argument marshalling only).
+
+Every function of the header is exposed under its own name on ``lib``; the
+helpers below only convert between numpy / torch objects and the C structures.
+All numerical work happens in libcarbox.so. Importing this module loads the
+library and raises if it has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libcarbox.so")
+
+CBX_OK = 0
+CBX_E_ARG, CBX_E_CUDA, CBX_E_NOMEM, CBX_E_TOO_LARGE = -1, -2, -3, -4
+CBX_CELL_OK, CBX_CELL_MAX_STEPS, CBX_CELL_H_UNDERFLOW, CBX_CELL_BAD_INPUT = 0, 1, 2, 5
+CBX_TWO_BODY, CBX_COSMIC_RAY, CBX_PHOTO = 0, 1, 2
+CBX_FP64, CBX_MIXED = 0, 1
+
+
+class cbx_species(C.Structure):
+    _fields_ = [("composition", C.c_int * 5), ("charge", C.c_int)]
+
+
+class cbx_reaction(C.Structure):
+    _fields_ = [("type", C.c_int), ("reac", C.c_int * 2), ("prod", C.c_int * 4),
+                ("alpha", C.c_double), ("beta", C.c_double), ("gamma", C.c_double)]
+
+
+class cbx_cell_params(C.Structure):
+    _fields_ = [("n_H", C.c_double), ("T", C.c_double), ("A_V", C.c_double), ("G0", C.c_double),
+                ("zeta", C.c_double)]
+
+
+class cbx_options(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("atol", C.c_double), ("max_steps", C.c_int), ("precision", C.c_int),
+                ("max_refine", C.c_int), ("reserved", C.c_int), ("refine_tol", C.c_double)]
+
+
+class cbx_cell_stats(C.Structure):
+    _fields_ = [(n, C.c_int) for n in ("steps", "attempts", "error_fails", "newton_fails", "rhs_evals",
+                                        "jac_evals", "lu_factors", "newton_iters", "refine_sweeps", "reserved")]
+
+
+STATS_FIELDS = [f for f, _ in cbx_cell_stats._fields_ if f != "reserved"]
+
+
+class cbx_netinfo(C.Structure):
+    _fields_ = [("S", C.c_int), ("R", C.c_int), ("nnz_jac", C.c_int), ("nnz_lu", C.c_int),
+                ("lu_flops", C.c_double), ("lu_flops_dense", C.c_double), ("smem_bytes_fp64", C.c_int),
+                ("smem_bytes_mixed", C.c_int)]
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"{_LIB_PATH} is not built: run paper_2511_10558_gb300.build.build() "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = C.CDLL(_LIB_PATH)
+    P = C.c_void_p
+    sig = {
+        "cbx_version": (C.c_int, []),
+        "cbx_last_error": (C.c_char_p, []),
+        "cbx_default_options": (C.c_int, [C.POINTER(cbx_options)]),
+        "cbx_network_create": (C.c_int, [C.POINTER(cbx_species), C.c_int, C.POINTER(cbx_reaction), C.c_int,
+                                         C.POINTER(P)]),
+        "cbx_network_destroy": (C.c_int, [P]),
+        "cbx_network_info": (C.c_int, [P, C.POINTER(cbx_netinfo)]),
+        "cbx_solve": (C.c_int, [P, P, P, C.c_int, C.c_double, C.c_double, C.POINTER(cbx_options), P, P, P, P]),
+        "cbx_solve_host": (C.c_int, [P, P, P, C.c_int, C.c_double, C.c_double, C.POINTER(cbx_options), P, P,
+                                     P, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+class CarboxError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__(f"{where} failed ({code}): {lib.cbx_last_error().decode()}")
+        self.code = code
+
+
+def check(code, where):
+    if code != CBX_OK:
+        raise CarboxError(code, where)
+
+
+def options(rtol=1e-4, atol=1e-20, max_steps=100000, precision=CBX_FP64, max_refine=5, refine_tol=1e-10):
+    o = cbx_options()
+    check(lib.cbx_default_options(C.byref(o)), "cbx_default_options")
+    o.rtol, o.atol, o.max_steps, o.precision = rtol, atol, max_steps, precision
+    o.max_refine, o.refine_tol = max_refine, refine_tol
+    return o
+
+
+class Network:
+    """Owns a cbx_network handle built from plain arrays (see synth.Network)."""
+
+    def __init__(self, composition, charge, rtype, reac, prod, alpha, beta, gamma):
+        S = len(charge)
+        R = len(rtype)
+        sp = (cbx_species * S)()
+        for i in range(S):
+            sp[i].composition[:] = [int(v) for v in composition[i]]
+            sp[i].charge = int(charge[i])
+        rx = (cbx_reaction * max(R, 1))()
+        for j in range(R):
+            rx[j].type = int(rtype[j])
+            rx[j].reac[:] = [int(v) for v in reac[j]]
+            rx[j].prod[:] = [int(v) for v in prod[j]]
+            rx[j].alpha, rx[j].beta, rx[j].gamma = float(alpha[j]), float(beta[j]), float(gamma[j])
+        h = C.c_void_p()
+        check(lib.cbx_network_create(sp, S, rx, R, C.byref(h)), "cbx_network_create")
+        self.handle = h
+        self.S, self.R = S, R
+
+    @classmethod
+    def from_synth(cls, net):
+        return cls(net.composition, net.charge, net.rtype, net.reac, net.prod, net.alpha, net.beta, net.gamma)
+
+    def info(self):
+        inf = cbx_netinfo()
+        check(lib.cbx_network_info(self.handle, C.byref(inf)), "cbx_network_info")
+        return {f: getattr(inf, f) for f, _ in cbx_netinfo._fields_}
+
+    def close(self):
+        if self.handle:
+            lib.cbx_network_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def solve(net, phi, x0, t0, t_end, opt=None, stream=None, x_out=None, status=None, stats=None):
+    """cbx_solve on torch CUDA tensors: phi [C, 5] f64, x0 [S, C] f64 (contiguous).
+
+    Returns (x_out [S, C], status [C] int32, stats [C, 10] int32 or None).
+    """
+    import torch
+    Cn = phi.shape[0]
+    assert phi.is_cuda and phi.dtype == torch.float64 and phi.is_contiguous() and phi.shape[1] == 5
+    assert x0.is_cuda and x0.dtype == torch.float64 and x0.is_contiguous() and tuple(x0.shape) == (net.S, Cn)
+    dev = phi.device
+    if x_out is None:
+        x_out = torch.empty((net.S, Cn), dtype=torch.float64, device=dev)
+    if status is None:
+        status = torch.empty(Cn, dtype=torch.int32, device=dev)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    o = opt if opt is not None else options()
+    check(lib.cbx_solve(net.handle, _ptr(phi), _ptr(x0), Cn, float(t0), float(t_end), C.byref(o),
+                        C.c_void_p(stream.cuda_stream), _ptr(x_out), _ptr(status), _ptr(stats)), "cbx_solve")
+    return x_out, status, stats
+
+
+def solve_host(net, phi, x0, t0, t_end, opt=None, stream=None, want_stats=False):
+    """cbx_solve_host on numpy arrays: phi [C, 5], x0 [S, C]; returns numpy results."""
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    Cn = phi.shape[0]
+    assert x0.shape == (net.S, Cn)
+    x_out = np.empty((net.S, Cn))
+    status = np.empty(Cn, dtype=np.int32)
+    stats = np.zeros((Cn, 10), dtype=np.int32) if want_stats else None
+    o = opt if opt is not None else options()
+    s = C.c_void_p(stream.cuda_stream) if stream is not None else None
+    check(lib.cbx_solve_host(net.handle, phi.ctypes.data_as(C.c_void_p), x0.ctypes.data_as(C.c_void_p), Cn,
+                             float(t0), float(t_end), C.byref(o), s, x_out.ctypes.data_as(C.c_void_p),
+                             status.ctypes.data_as(C.c_void_p),
+                             stats.ctypes.data_as(C.c_void_p) if stats is not None else None), "cbx_solve_host")
+    return x_out, status, stats

@@ -1,0 +1,277 @@
+// C ABI glue: argument checks, device upload of compiled networks, workspace
+// and launches. Every entry point returns a CBX_* code and records a message.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace cbx;
+
+struct cbx_network {
+  HostNet host;
+  DevNet dev;
+  void* dbuf = nullptr;  // one device allocation holding every table
+  int device = 0;
+  std::mutex mu;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(CBX_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Pack int and double tables into one device buffer.
+struct Packer {
+  std::vector<unsigned char> bytes;
+  template <typename T>
+  size_t add(const std::vector<T>& v) {
+    size_t off = (bytes.size() + 255) & ~size_t(255);
+    bytes.resize(off + v.size() * sizeof(T) + 1);
+    if (!v.empty()) memcpy(bytes.data() + off, v.data(), v.size() * sizeof(T));
+    return off;
+  }
+};
+
+int check_options(const cbx_options& o) {
+  if (!(o.rtol > 0.0) || !std::isfinite(o.rtol)) return fail(CBX_E_ARG, "rtol must be finite and > 0");
+  if (!(o.atol >= 0.0) || !std::isfinite(o.atol)) return fail(CBX_E_ARG, "atol must be finite and >= 0");
+  if (o.max_steps < 1) return fail(CBX_E_ARG, "max_steps must be >= 1");
+  if (o.precision != CBX_FP64 && o.precision != CBX_MIXED) return fail(CBX_E_ARG, "precision must be CBX_FP64 or CBX_MIXED");
+  if (o.precision == CBX_MIXED && o.max_refine < 1) return fail(CBX_E_ARG, "max_refine must be >= 1");
+  if (!(o.refine_tol >= 0.0)) return fail(CBX_E_ARG, "refine_tol must be >= 0");
+  return CBX_OK;
+}
+
+// Upload the compiled tables to the current device (once per network).
+int upload(cbx_network* n) {
+  std::lock_guard<std::mutex> lock(n->mu);
+  if (n->dbuf) return CBX_OK;
+  const HostNet& h = n->host;
+  Packer pk;
+  size_t o_rtype = pk.add(h.rtype), o_alpha = pk.add(h.alpha), o_beta = pk.add(h.beta),
+         o_gamma = pk.add(h.gamma), o_ra = pk.add(h.ra), o_rb = pk.add(h.rb), o_seg = pk.add(h.seg_ptr),
+         o_sps = pk.add(h.spec_seg), o_ent = pk.add(h.rhs_ent), o_jrow = pk.add(h.jrow),
+         o_jcol = pk.add(h.jcol), o_jrp = pk.add(h.jrow_ptr), o_jtp = pk.add(h.jterm_ptr),
+         o_jt = pk.add(h.jterm), o_plp = pk.add(h.piv_lptr), o_pl = pk.add(h.piv_l),
+         o_pup = pk.add(h.piv_uptr), o_pu = pk.add(h.piv_u), o_perm = pk.add(h.perm);
+  cudaGetDevice(&n->device);
+  cudaError_t e = cudaMalloc(&n->dbuf, pk.bytes.size());
+  if (e != cudaSuccess) {
+    n->dbuf = nullptr;
+    return cuda_fail(e, "cudaMalloc(network tables)");
+  }
+  e = cudaMemcpy(n->dbuf, pk.bytes.data(), pk.bytes.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(n->dbuf);
+    n->dbuf = nullptr;
+    return cuda_fail(e, "cudaMemcpy(network tables)");
+  }
+  unsigned char* b = (unsigned char*)n->dbuf;
+  DevNet& d = n->dev;
+  d.S = h.S;
+  d.R = h.R;
+  d.nnzJ = h.nnzJ;
+  d.nseg = h.nseg;
+  d.rtype = (const int*)(b + o_rtype);
+  d.alpha = (const double*)(b + o_alpha);
+  d.beta = (const double*)(b + o_beta);
+  d.gamma = (const double*)(b + o_gamma);
+  d.ra = (const int*)(b + o_ra);
+  d.rb = (const int*)(b + o_rb);
+  d.seg_ptr = (const int*)(b + o_seg);
+  d.spec_seg = (const int*)(b + o_sps);
+  d.rhs_ent = (const int*)(b + o_ent);
+  d.jrow = (const int*)(b + o_jrow);
+  d.jcol = (const int*)(b + o_jcol);
+  d.jrow_ptr = (const int*)(b + o_jrp);
+  d.jterm_ptr = (const int*)(b + o_jtp);
+  d.jterm = (const int*)(b + o_jt);
+  d.piv_lptr = (const int*)(b + o_plp);
+  d.piv_l = (const int*)(b + o_pl);
+  d.piv_uptr = (const int*)(b + o_pup);
+  d.piv_u = (const int*)(b + o_pu);
+  d.perm = (const int*)(b + o_perm);
+  return CBX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cbx_version(void) { return CBX_VERSION; }
+
+const char* cbx_last_error(void) { return g_err.c_str(); }
+
+int cbx_default_options(cbx_options* out) {
+  if (!out) return fail(CBX_E_ARG, "out is NULL");
+  memset(out, 0, sizeof *out);
+  out->rtol = 1e-4;
+  out->atol = 1e-20;
+  out->max_steps = 100000;
+  out->precision = CBX_FP64;
+  out->max_refine = 5;
+  out->refine_tol = 1e-10;
+  return CBX_OK;
+}
+
+int cbx_network_create(const cbx_species* species, int S, const cbx_reaction* reactions, int R,
+                       cbx_network** out) {
+  if (!out) return fail(CBX_E_ARG, "out is NULL");
+  *out = nullptr;
+  cbx_network* n = new (std::nothrow) cbx_network();
+  if (!n) return fail(CBX_E_NOMEM, "host allocation failed");
+  std::string msg = compile_network(species, S, reactions, R, &n->host);
+  if (!msg.empty()) {
+    delete n;
+    return fail(CBX_E_ARG, msg);
+  }
+  int dc = 0;
+  if (cudaGetDeviceCount(&dc) == cudaSuccess && dc > 0) {
+    const int rc = upload(n);
+    if (rc != CBX_OK) {
+      delete n;
+      return rc;
+    }
+  } else {
+    cudaGetLastError();
+  }
+  *out = n;
+  return CBX_OK;
+}
+
+int cbx_network_destroy(cbx_network* net) {
+  if (!net) return CBX_OK;
+  if (net->dbuf) cudaFree(net->dbuf);
+  delete net;
+  return CBX_OK;
+}
+
+int cbx_network_info(const cbx_network* net, cbx_netinfo* out) {
+  if (!net || !out) return fail(CBX_E_ARG, "NULL argument");
+  const HostNet& h = net->host;
+  out->S = h.S;
+  out->R = h.R;
+  out->nnz_jac = h.nnzJ;
+  out->nnz_lu = h.nnzLU;
+  out->lu_flops = h.lu_flops;
+  out->lu_flops_dense = 2.0 * h.S * (double)h.S * h.S / 3.0;
+  out->smem_bytes_fp64 = (int)smem_bytes(h.S, h.R, h.nseg, false);
+  out->smem_bytes_mixed = (int)smem_bytes(h.S, h.R, h.nseg, true);
+  return CBX_OK;
+}
+
+int cbx_solve(cbx_network* net, const cbx_cell_params* phi, const double* x0, int C, double t0,
+              double t_end, const cbx_options* opt, void* stream, double* x_out, int* cell_status,
+              cbx_cell_stats* stats) {
+  if (!net) return fail(CBX_E_ARG, "net is NULL");
+  if (C < 0) return fail(CBX_E_ARG, "C must be >= 0");
+  if (C > 0 && (!phi || !x0 || !x_out || !cell_status)) return fail(CBX_E_ARG, "NULL array with C > 0");
+  if (!std::isfinite(t0) || !std::isfinite(t_end) || t_end < t0) return fail(CBX_E_ARG, "need finite t0 <= t_end");
+  cbx_options o;
+  cbx_default_options(&o);
+  if (opt) o = *opt;
+  int rc = check_options(o);
+  if (rc) return rc;
+  if (C == 0) return CBX_OK;
+  rc = upload(net);
+  if (rc) return rc;
+  const HostNet& h = net->host;
+  const bool mixed = o.precision == CBX_MIXED;
+  const int occ = solver_occupancy(h.S, h.R, h.nseg, mixed);
+  if (occ < 1) {
+    char m[160];
+    snprintf(m, sizeof m, "network (S=%d, R=%d) needs %zu B of shared memory per CTA; the device allows %zu",
+             h.S, h.R, smem_bytes(h.S, h.R, h.nseg, mixed), device_smem_optin());
+    return fail(CBX_E_TOO_LARGE, m);
+  }
+  const int grid = std::min(C, occ * device_sm_count());
+  cudaStream_t st = (cudaStream_t)stream;
+  SolveArgs a{};
+  a.net = net->dev;
+  a.phi = phi;
+  a.x0 = x0;
+  a.C = C;
+  a.t0 = t0;
+  a.t_end = t_end;
+  a.rtol = o.rtol;
+  a.atol = o.atol;
+  a.newton_tol = std::max(10.0 * 2.220446049250313e-16 / o.rtol, std::min(0.03, std::sqrt(o.rtol)));
+  a.refine_tol = o.refine_tol;
+  a.max_steps = o.max_steps;
+  a.max_refine = o.max_refine;
+  for (int q = 0; q < kMaxOrder + 2; ++q) {
+    double g = 0.0;
+    for (int j = 1; j <= q; ++j) g += 1.0 / j;
+    a.gam[q] = g;
+  }
+  a.x_out = x_out;
+  a.status = cell_status;
+  a.stats = stats;
+  a.ws_stride = workspace_doubles(h.S, h.R, h.nnzJ);
+  const size_t ws_bytes = (size_t)grid * a.ws_stride * sizeof(double) + 256;
+  void* ws = nullptr;
+  cudaError_t e = cudaMallocAsync(&ws, ws_bytes, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(workspace)");
+  a.ws = (double*)ws;
+  a.counter = (int*)((char*)ws + (size_t)grid * a.ws_stride * sizeof(double));
+  e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = (cudaError_t)launch_solver(a, mixed, grid, stream);
+  cudaError_t e2 = cudaFreeAsync(ws, st);
+  if (e != cudaSuccess) return cuda_fail(e, "solver launch");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync(workspace)");
+  return CBX_OK;
+}
+
+int cbx_solve_host(cbx_network* net, const cbx_cell_params* phi, const double* x0, int C, double t0,
+                   double t_end, const cbx_options* opt, void* stream, double* x_out,
+                   int* cell_status, cbx_cell_stats* stats) {
+  if (!net) return fail(CBX_E_ARG, "net is NULL");
+  if (C < 0) return fail(CBX_E_ARG, "C must be >= 0");
+  if (C > 0 && (!phi || !x0 || !x_out || !cell_status)) return fail(CBX_E_ARG, "NULL array with C > 0");
+  if (C == 0) return cbx_solve(net, phi, x0, 0, t0, t_end, opt, stream, x_out, cell_status, stats);
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t S = net->host.S;
+  const size_t b_phi = C * sizeof(cbx_cell_params), b_x = S * C * sizeof(double), b_st = C * sizeof(int),
+               b_stats = stats ? C * sizeof(cbx_cell_stats) : 0;
+  char* d = nullptr;
+  const size_t o_x0 = (b_phi + 255) & ~size_t(255), o_xo = o_x0 + ((b_x + 255) & ~size_t(255)),
+               o_st = o_xo + ((b_x + 255) & ~size_t(255)), o_stats = o_st + ((b_st + 255) & ~size_t(255)),
+               total = o_stats + b_stats + 256;
+  cudaError_t e = cudaMallocAsync((void**)&d, total, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(host-call buffers)");
+  int rc = CBX_OK;
+  e = cudaMemcpyAsync(d, phi, b_phi, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d + o_x0, x0, b_x, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    rc = cuda_fail(e, "cudaMemcpyAsync(H2D)");
+  } else {
+    rc = cbx_solve(net, (const cbx_cell_params*)d, (const double*)(d + o_x0), C, t0, t_end, opt, stream,
+                   (double*)(d + o_xo), (int*)(d + o_st), stats ? (cbx_cell_stats*)(d + o_stats) : nullptr);
+    if (rc == CBX_OK) {
+      e = cudaMemcpyAsync(x_out, d + o_xo, b_x, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(cell_status, d + o_st, b_st, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess && stats) e = cudaMemcpyAsync(stats, d + o_stats, b_stats, cudaMemcpyDeviceToHost, st);
+      if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync(D2H)");
+    }
+  }
+  cudaFreeAsync(d, st);
+  e = cudaStreamSynchronize(st);
+  if (rc == CBX_OK && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,88 @@
+// Internal declarations shared by the host network compiler, the kernels and
+// the C ABI glue. Not part of the public interface (include/carbox.h).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "carbox.h"
+
+namespace cbx {
+
+constexpr int kMaxOrder = 5;           // BDF orders 1..5
+constexpr int kDiffRows = kMaxOrder + 3;  // difference array rows D[0..q+2]
+constexpr int kSegLen = 16;            // entries per right-hand-side gather segment
+
+// Device view of a compiled network: all species indices are internal
+// (fill-reducing order); perm maps internal -> user index.
+struct DevNet {
+  int S, R, nnzJ, nseg;
+  const int* rtype;      // [R]
+  const double* alpha;   // [R]
+  const double* beta;    // [R]
+  const double* gamma;   // [R]
+  const int* ra;         // [R] first reactant
+  const int* rb;         // [R] second reactant or -1
+  const int* seg_ptr;    // [nseg+1] entry range of each gather segment
+  const int* spec_seg;   // [S+1] segment range of each species
+  const int* rhs_ent;    // (reaction << 1) | negative, |nu| copies per term
+  const int* jrow;       // [nnzJ] row of each Jacobian slot (slots sorted by row, col)
+  const int* jcol;       // [nnzJ] column
+  const int* jrow_ptr;   // [S+1] CSR row pointer over the slots
+  const int* jterm_ptr;  // [nnzJ+1] term range per slot
+  const int* jterm;      // ((2 reaction + reactant slot) << 1) | negative
+  const int* piv_lptr;   // [S+1] range of rows i > k with L(i,k) structurally non-zero
+  const int* piv_l;
+  const int* piv_uptr;   // [S+1] range of columns j > k with U(k,j) structurally non-zero
+  const int* piv_u;
+  const int* perm;       // [S] internal -> user species index
+};
+
+// Host-side compiled network.
+struct HostNet {
+  int S = 0, R = 0, nnzJ = 0, nnzLU = 0, nseg = 0;
+  double lu_flops = 0;
+  std::vector<int> perm, iperm;
+  std::vector<int> rtype, ra, rb;
+  std::vector<double> alpha, beta, gamma;
+  std::vector<int> seg_ptr, spec_seg, rhs_ent;
+  std::vector<int> jrow, jcol, jrow_ptr, jterm_ptr, jterm;
+  std::vector<int> piv_lptr, piv_l, piv_uptr, piv_u;
+};
+
+// Returns "" on success, else an error message.
+std::string compile_network(const cbx_species* sp, int S, const cbx_reaction* rx, int R, HostNet* out);
+
+// Minimum-degree ordering of a symmetric pattern (adjacency as dense bool, S x S).
+std::vector<int> minimum_degree_order(const std::vector<uint8_t>& sym, int S);
+
+struct SolveArgs {
+  DevNet net;
+  const cbx_cell_params* phi;
+  const double* x0;
+  int C;
+  double t0, t_end;
+  double rtol, atol, newton_tol, refine_tol;
+  int max_steps, max_refine;
+  double gam[kMaxOrder + 2];  // gamma_q = sum_{j=1..q} 1/j
+  double* x_out;
+  int* status;
+  cbx_cell_stats* stats;
+  double* ws;      // per-CTA workspace, ws_stride doubles per CTA
+  long long ws_stride;
+  int* counter;    // next-cell counter, zero before the launch
+};
+
+// Shared-memory bytes per CTA of the smem solver (mixed = FP32 matrix).
+size_t smem_bytes(int S, int R, int nseg, bool mixed);
+// Per-CTA global workspace, in doubles.
+long long workspace_doubles(int S, int R, int nnzJ);
+// Launch the smem solver; returns a cudaError_t value.
+int launch_solver(const SolveArgs& a, bool mixed, int grid, void* stream);
+// CTAs per SM the solver can keep resident (0 if it cannot launch).
+int solver_occupancy(int S, int R, int nseg, bool mixed);
+int device_sm_count();
+size_t device_smem_optin();
+
+}  // namespace cbx

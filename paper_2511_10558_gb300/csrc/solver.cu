@@ -1,0 +1,697 @@
+// Persistent per-cell BDF solver for sm_103a.
+//
+// One CTA integrates one cell at a time from t0 to t_end entirely on chip and
+// then takes the next cell from an atomic counter (cells finish at different
+// step counts; the counter keeps every SM busy until the batch is done). The
+// cell's Newton matrix M = I - cJ lives densely in shared memory (the symbolic
+// LU fill of these networks is ~80 % dense), the network tables are read-only
+// and shared by all CTAs through L1/L2, and the per-cell FP64 Jacobian values
+// sit in a per-CTA global workspace (L2-resident).
+//
+// The integrator is the variable-order (1..5), quasi-constant-step BDF in
+// backward-difference form (Shampine & Reichelt 1997, kappa = 0) - the BDF
+// family that Sec. 1 of the paper names as the field's stiff integrator - with
+// a simplified Newton iteration on (I - cJ) dy = c f(y) - psi - d, c = h/gamma_q.
+// Constants and policies:
+//   Newton        <= 4 iterations; rate = |dy_k| / |dy_{k-1}|; fail when
+//                 rate >= 1 or rate^(4-k)/(1-rate) |dy_k| > tol_N; converged
+//                 when |dy| = 0 or rate/(1-rate) |dy| < tol_N
+//   norms         weighted RMS, weights 1/(atol + rtol |y|): predictor for
+//                 Newton, result for the error test
+//   error test    |d/(q+1)| <= 1; on failure h *= max(0.2, 0.9 err^(-1/(q+1)))
+//   Newton fail   re-evaluate J if it is stale, else h *= 0.5
+//   step/order    after q+1 equal steps: estimates at q-1, q, q+1, the largest
+//                 factor err_k^(-1/(k+1)) wins; h *= min(10, 0.9 factor)
+//   LU            refactored whenever h or J changed
+//   initial step  Hairer, Norsett & Wanner I, Sec. II.4 (order 1)
+//   limits        max_steps attempts; h < 10 ulp(t) -> H_UNDERFLOW
+//
+// FP64 on GB300 retires about 2 FMA per clock per SM, so one warp-wide FP64
+// instruction holds the SM's FP64 pipe for ~16 clocks whatever its active
+// lanes: the vector loops below keep lanes full, and scalar FP64 work (pow,
+// the rescale matrix) runs on one thread or one warp and is broadcast.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+
+#include "internal.h"
+
+namespace cbx {
+
+constexpr int NT = 256;
+constexpr int NW = NT / 32;
+constexpr int kNewtonMaxIter = 4;
+constexpr int kMaxColRegs = 8;  // columns per lane in the LU update: S <= 256
+constexpr unsigned FULL = 0xffffffffu;
+
+// ---------------------------------------------------------------- helpers
+
+// Deterministic block sum: warp trees, then the NW partials in a fixed order.
+// Every thread returns the same value. Contains two barriers.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int i = 0; i < NW; ++i) s += red[i];
+    if (threadIdx.x == 0) red[NW] = s;
+  }
+  __syncthreads();
+  const double s = red[NW];
+  __syncthreads();
+  return s;
+}
+
+// sqrt(mean((a * v_i * w_i)^2)), w = reciprocal weights
+__device__ double wrms(const double* v, const double* w, double a, int S, double* red) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < S; i += NT) {
+    const double t = a * v[i] * w[i];
+    acc = fma(t, t, acc);
+  }
+  return sqrt(block_sum(acc, red) / S);
+}
+
+// One thread computes pow(x, y); everybody gets it.
+__device__ double uniform_pow(double x, double y, double* slot) {
+  if (threadIdx.x == 0) *slot = pow(x, y);
+  __syncthreads();
+  const double v = *slot;
+  __syncthreads();
+  return v;
+}
+
+__device__ __forceinline__ double growth(double err, int p, double* slot) {
+  return err == 0.0 ? INFINITY : uniform_pow(err, -1.0 / p, slot);
+}
+
+// ---------------------------------------------------------------- chemistry
+
+// kappa_j of one cell (Sec. 2 two-body and cosmic-ray forms, App. B.1 photo
+// form); two-body values carry the n_H factor of x = n / n_H.
+__device__ void rate_coefficients(const DevNet& n, const cbx_cell_params& p, double* kap) {
+  const double lnT = log(p.T / 300.0);
+  const double invT = 1.0 / p.T;
+  for (int j = threadIdx.x; j < n.R; j += NT) {
+    const int t = n.rtype[j];
+    double k;
+    if (t == CBX_TWO_BODY)
+      k = n.alpha[j] * exp(n.beta[j] * lnT - n.gamma[j] * invT) * p.n_H;
+    else if (t == CBX_COSMIC_RAY)
+      k = n.alpha[j] * p.zeta;
+    else
+      k = n.alpha[j] * p.G0 * exp(-n.gamma[j] * p.A_V);
+    kap[j] = k;
+  }
+}
+
+// f = nu r(y): reaction rates into r, signed segment sums into part, then
+// per-species sums of the segments (fixed order: bitwise reproducible).
+__device__ void rhs(const DevNet& n, const double* __restrict__ kap, const double* y, double* f,
+                    double* r, double* part) {
+  for (int j = threadIdx.x; j < n.R; j += NT) {
+    const int b = __ldg(n.rb + j);
+    double v = kap[j] * y[__ldg(n.ra + j)];
+    if (b >= 0) v *= y[b];
+    r[j] = v;
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < n.nseg; s += NT) {
+    double acc = 0.0;
+    const int e1 = __ldg(n.seg_ptr + s + 1);
+    for (int e = __ldg(n.seg_ptr + s); e < e1; ++e) {
+      const int t = __ldg(n.rhs_ent + e);
+      const double v = r[t >> 1];
+      acc += (t & 1) ? -v : v;
+    }
+    part[s] = acc;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n.S; i += NT) {
+    double acc = 0.0;
+    const int s1 = __ldg(n.spec_seg + i + 1);
+    for (int s = __ldg(n.spec_seg + i); s < s1; ++s) acc += part[s];
+    f[i] = acc;
+  }
+  __syncthreads();
+}
+
+// Analytic Jacobian values per slot: J(i,l) = sum nu_ij dr_j/dx_l, with the
+// reaction partials g[2j+s] = d r_j / d x(reactant s).
+__device__ void jacobian(const DevNet& n, const double* __restrict__ kap, const double* y, double* g,
+                         double* Jv) {
+  for (int j = threadIdx.x; j < n.R; j += NT) {
+    const int b = n.rb[j];
+    const double k = kap[j];
+    if (b >= 0) {
+      g[2 * j] = k * y[b];
+      g[2 * j + 1] = k * y[n.ra[j]];
+    } else {
+      g[2 * j] = k;
+      g[2 * j + 1] = 0.0;
+    }
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < n.nnzJ; s += NT) {
+    double acc = 0.0;
+    const int e1 = n.jterm_ptr[s + 1];
+    for (int e = n.jterm_ptr[s]; e < e1; ++e) {
+      const int t = n.jterm[e];
+      const double v = g[t >> 1];
+      acc += (t & 1) ? -v : v;
+    }
+    Jv[s] = acc;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- linear algebra
+
+template <typename LT>
+__device__ void build_matrix(const DevNet& n, const double* Jv, double c, LT* M) {
+  const int S = n.S;
+  for (int idx = threadIdx.x; idx < S * S; idx += NT) M[idx] = LT(0);
+  __syncthreads();
+  for (int s = threadIdx.x; s < n.nnzJ; s += NT) {
+    const int i = n.jrow[s], l = n.jcol[s];
+    const double cj = c * Jv[s];
+    M[i * S + l] = (LT)(i == l ? 1.0 - cj : -cj);
+  }
+  __syncthreads();
+}
+
+// In-place LU without pivoting on the static fill pattern: per pivot k, one
+// warp scales the L column by the reciprocal pivot; then warps take the rows
+// of L(:,k), lanes the columns of U(k,:) held in registers.
+template <typename LT>
+__device__ void lu_factor(const DevNet& n, LT* M, LT* invd) {
+  const int S = n.S;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = 0; k < S; ++k) {
+    const int l0 = __ldg(n.piv_lptr + k), l1 = __ldg(n.piv_lptr + k + 1);
+    if (w == 0) {
+      const LT inv = LT(1) / M[k * S + k];
+      if (lane == 0) invd[k] = inv;
+      for (int e = l0 + lane; e < l1; e += 32) {
+        const int i = __ldg(n.piv_l + e);
+        M[i * S + k] *= inv;
+      }
+    }
+    __syncthreads();
+    const int u0 = __ldg(n.piv_uptr + k), nu = __ldg(n.piv_uptr + k + 1) - u0;
+    if (l1 > l0 && nu > 0) {
+      int jc[kMaxColRegs];
+      LT uv[kMaxColRegs];
+#pragma unroll
+      for (int m = 0; m < kMaxColRegs; ++m) {
+        const int b = lane + 32 * m;
+        jc[m] = b < nu ? __ldg(n.piv_u + u0 + b) : 0;
+        uv[m] = b < nu ? M[k * S + jc[m]] : LT(0);
+      }
+      for (int e = l0 + w; e < l1; e += NW) {
+        const int i = __ldg(n.piv_l + e);
+        LT* row = M + i * S;
+        const LT l = row[k];
+#pragma unroll
+        for (int m = 0; m < kMaxColRegs; ++m) {
+          if (lane + 32 * m < nu) row[jc[m]] -= l * uv[m];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// v <- L^{-1} v (unit lower), blocks of 32: one warp solves the diagonal block
+// with shuffles, then every thread updates one row below it.
+template <typename LT>
+__device__ void forward_solve(const LT* M, int S, LT* v) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int kb = 0; kb < S; kb += 32) {
+    const int nb = min(32, S - kb);
+    if (w == 0) {
+      LT val = lane < nb ? v[kb + lane] : LT(0);
+      for (int k = 0; k < nb - 1; ++k) {
+        const LT yk = __shfl_sync(FULL, val, k);
+        if (lane > k && lane < nb) val -= M[(kb + lane) * S + kb + k] * yk;
+      }
+      if (lane < nb) v[kb + lane] = val;
+    }
+    __syncthreads();
+    for (int i = kb + nb + threadIdx.x; i < S; i += NT) {
+      LT acc = v[i];
+      const LT* row = M + i * S + kb;
+      for (int k = 0; k < nb; ++k) acc -= row[k] * v[kb + k];
+      v[i] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// v <- U^{-1} v (upper, reciprocal diagonal in invd), blocks from the bottom.
+template <typename LT>
+__device__ void backward_solve(const LT* M, const LT* invd, int S, LT* v) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int ke = S; ke > 0; ke -= 32) {
+    const int kb = max(0, ke - 32), nb = ke - kb;
+    if (w == 0) {
+      LT val = lane < nb ? v[kb + lane] : LT(0);
+      for (int k = nb - 1; k >= 0; --k) {
+        if (lane == k) val *= invd[kb + k];
+        const LT xk = __shfl_sync(FULL, val, k);
+        if (lane < k) val -= M[(kb + lane) * S + kb + k] * xk;
+      }
+      if (lane < nb) v[kb + lane] = val;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kb; i += NT) {
+      LT acc = v[i];
+      const LT* row = M + i * S + kb;
+      for (int k = 0; k < nb; ++k) acc -= row[k] * v[kb + k];
+      v[i] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- shared layout
+
+struct Smem {
+  void* M;
+  void* invd;
+  double *D, *y, *yp, *dv, *f, *wsc, *psi, *dy, *w, *tmp, *r, *part, *red, *Tm;
+  float* v32;
+};
+
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+__host__ __device__ inline size_t layout(int S, int R, int nseg, bool mixed, unsigned char* base, Smem* s) {
+  const size_t lt = mixed ? sizeof(float) : sizeof(double);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    unsigned char* p = base ? base + off : nullptr;
+    off += align16(bytes);
+    return p;
+  };
+  Smem t;
+  t.M = take((size_t)S * S * lt);
+  t.invd = take((size_t)S * lt);
+  t.D = (double*)take((size_t)kDiffRows * S * 8);
+  t.y = (double*)take(S * 8);
+  t.yp = (double*)take(S * 8);
+  t.dv = (double*)take(S * 8);
+  t.f = (double*)take(S * 8);
+  t.wsc = (double*)take(S * 8);
+  t.psi = (double*)take(S * 8);
+  t.dy = (double*)take(S * 8);
+  t.w = (double*)take(S * 8);
+  t.tmp = (double*)take(S * 8);
+  t.r = (double*)take((size_t)R * 8);
+  t.part = (double*)take((size_t)nseg * 8);
+  t.red = (double*)take(64 * 8);
+  t.Tm = (double*)take(kMaxOrder * kMaxOrder * 8);
+  t.v32 = (float*)take(mixed ? S * 4 : 0);
+  if (s) *s = t;
+  return off;
+}
+
+size_t smem_bytes(int S, int R, int nseg, bool mixed) { return layout(S, R, nseg, mixed, nullptr, nullptr); }
+
+long long workspace_doubles(int S, int R, int nnzJ) {
+  (void)S;
+  const long long n = 3LL * R + nnzJ;
+  return (n + 31) / 32 * 32;
+}
+
+// ---------------------------------------------------------------- BDF pieces
+
+// D[1..q] <- T(rho) D[1..q], T[k][j] = sum_i (-1)^i C(k,i) C(-i rho + j - 1, j):
+// the differences of the interpolating polynomial on the new spacing. The
+// q x q matrix is computed by one warp (lane = (k, j)).
+__device__ void rescale(double* D, int S, int q, double rho, double* Tm) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    if (lane < q * q) {
+      const int k = lane / q + 1, j = lane % q + 1;
+      double acc = 0.0;
+      double binom = 1.0;  // C(k, i)
+      for (int i = 0; i <= k; ++i) {
+        const double s = -i * rho;
+        double nb = 1.0;
+        for (int m = 0; m < j; ++m) nb *= (s + m) / (m + 1);
+        const double term = ((i & 1) ? -binom : binom) * nb;
+        acc += term;
+        binom = binom * (k - i) / (i + 1);
+      }
+      Tm[(k - 1) * kMaxOrder + (j - 1)] = acc;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < S; i += NT) {
+    double old[kMaxOrder];
+#pragma unroll
+    for (int j = 0; j < kMaxOrder; ++j) old[j] = j < q ? D[(j + 1) * S + i] : 0.0;
+    for (int k = 0; k < q; ++k) {
+      double acc = 0.0;
+#pragma unroll
+      for (int j = 0; j < kMaxOrder; ++j)
+        if (j < q) acc = fma(Tm[k * kMaxOrder + j], old[j], acc);
+      D[(k + 1) * S + i] = acc;
+    }
+  }
+  __syncthreads();
+}
+
+template <typename LT>
+struct Cell {
+  const SolveArgs& a;
+  const DevNet& n;
+  Smem& s;
+  double* kap;
+  double* g;
+  double* Jv;
+  cbx_cell_stats st;
+};
+
+// Solve (I - cJ) dy = w with the factored matrix in shared memory.
+template <typename LT>
+__device__ void linear_solve(Cell<LT>& c, double cc, const double* w, double* dy);
+
+template <>
+__device__ void linear_solve<double>(Cell<double>& c, double cc, const double* w, double* dy) {
+  const int S = c.n.S;
+  for (int i = threadIdx.x; i < S; i += NT) dy[i] = w[i];
+  __syncthreads();
+  forward_solve<double>((const double*)c.s.M, S, dy);
+  backward_solve<double>((const double*)c.s.M, (const double*)c.s.invd, S, dy);
+}
+
+// FP32 LU solve, then FP64 residual w - (dy - c J dy) against the FP64
+// Jacobian and FP32 correction solves until the weighted RMS of the
+// correction is <= refine_tol or max_refine sweeps.
+template <>
+__device__ void linear_solve<float>(Cell<float>& c, double cc, const double* w, double* dy) {
+  const int S = c.n.S;
+  const float* M = (const float*)c.s.M;
+  const float* invd = (const float*)c.s.invd;
+  float* v = c.s.v32;
+  for (int i = threadIdx.x; i < S; i += NT) v[i] = (float)w[i];
+  __syncthreads();
+  forward_solve<float>(M, S, v);
+  backward_solve<float>(M, invd, S, v);
+  for (int i = threadIdx.x; i < S; i += NT) dy[i] = (double)v[i];
+  __syncthreads();
+  for (int sweep = 0; sweep < c.a.max_refine; ++sweep) {
+    for (int i = threadIdx.x; i < S; i += NT) {
+      double acc = 0.0;
+      const int e1 = c.n.jrow_ptr[i + 1];
+      for (int e = c.n.jrow_ptr[i]; e < e1; ++e) acc = fma(c.Jv[e], dy[c.n.jcol[e]], acc);
+      const double res = w[i] - (dy[i] - cc * acc);
+      v[i] = (float)res;
+    }
+    __syncthreads();
+    forward_solve<float>(M, S, v);
+    backward_solve<float>(M, invd, S, v);
+    double sq = 0.0;
+    for (int i = threadIdx.x; i < S; i += NT) {
+      const double corr = (double)v[i];
+      dy[i] += corr;
+      const double t = corr * c.s.wsc[i];
+      sq = fma(t, t, sq);
+    }
+    c.st.refine_sweeps++;
+    const double nrm = sqrt(block_sum(sq, c.s.red) / S);
+    if (!(nrm > c.a.refine_tol)) break;
+  }
+}
+
+template <typename LT>
+__device__ void factor(Cell<LT>& c, double cc) {
+  build_matrix<LT>(c.n, c.Jv, cc, (LT*)c.s.M);
+  lu_factor<LT>(c.n, (LT*)c.s.M, (LT*)c.s.invd);
+  c.st.lu_factors++;
+}
+
+// Simplified Newton on d - c f(yp + d) + psi = 0. Leaves y = yp + d, dv = d.
+template <typename LT>
+__device__ bool newton(Cell<LT>& c, double cc, int* iters) {
+  const int S = c.n.S;
+  Smem& s = c.s;
+  for (int i = threadIdx.x; i < S; i += NT) {
+    s.y[i] = s.yp[i];
+    s.dv[i] = 0.0;
+  }
+  __syncthreads();
+  double dy_old = 0.0, rate = 0.0;
+  bool conv = false;
+  for (int k = 0; k < kNewtonMaxIter; ++k) {
+    *iters = k + 1;
+    rhs(c.n, c.kap, s.y, s.f, s.r, s.part);
+    c.st.rhs_evals++;
+    int bad = 0;
+    for (int i = threadIdx.x; i < S; i += NT) bad |= !isfinite(s.f[i]);
+    if (__syncthreads_or(bad)) break;
+    for (int i = threadIdx.x; i < S; i += NT) s.w[i] = cc * s.f[i] - s.psi[i] - s.dv[i];
+    __syncthreads();
+    linear_solve<LT>(c, cc, s.w, s.dy);
+    const double dyn = wrms(s.dy, s.wsc, 1.0, S, s.red);
+    if (k > 0) {
+      rate = dyn / dy_old;
+      double rp = 1.0;
+      for (int m = 0; m < kNewtonMaxIter - k; ++m) rp *= rate;
+      if (rate >= 1.0 || rp / (1.0 - rate) * dyn > c.a.newton_tol) break;
+    }
+    for (int i = threadIdx.x; i < S; i += NT) {
+      s.y[i] += s.dy[i];
+      s.dv[i] += s.dy[i];
+    }
+    __syncthreads();
+    if (dyn == 0.0 || (k > 0 && rate / (1.0 - rate) * dyn < c.a.newton_tol)) {
+      conv = true;
+      break;
+    }
+    dy_old = dyn;
+  }
+  return conv;
+}
+
+template <typename LT>
+__device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
+  const DevNet& n = a.net;
+  const int S = n.S;
+  Cell<LT> c{a, n, s, ws, ws + n.R, ws + 3 * n.R, {}};
+  const cbx_cell_params p = a.phi[cell];
+  int status = CBX_CELL_OK;
+  for (int i = threadIdx.x; i < S; i += NT) s.y[i] = a.x0[(size_t)__ldg(n.perm + i) * a.C + cell];
+  if (!(p.n_H > 0.0) || !(p.T > 0.0) || !isfinite(p.n_H) || !isfinite(p.T) || !isfinite(p.A_V) ||
+      !isfinite(p.G0) || !isfinite(p.zeta)) {
+    status = CBX_CELL_BAD_INPUT;
+    __syncthreads();
+    for (int i = threadIdx.x; i < S; i += NT) a.x_out[(size_t)__ldg(n.perm + i) * a.C + cell] = s.y[i];
+  } else {
+    rate_coefficients(n, p, c.kap);
+    __syncthreads();
+    const double rtol = a.rtol, atol = a.atol, t_end = a.t_end;
+    double* D = s.D;
+    // f0 and the initial step (Hairer, Norsett & Wanner I, II.4, p = 1)
+    rhs(n, c.kap, s.y, s.f, s.r, s.part);
+    c.st.rhs_evals++;
+    for (int i = threadIdx.x; i < S; i += NT) s.wsc[i] = 1.0 / (atol + rtol * fabs(s.y[i]));
+    __syncthreads();
+    const double d0 = wrms(s.y, s.wsc, 1.0, S, s.red);
+    const double d1 = wrms(s.f, s.wsc, 1.0, S, s.red);
+    const double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
+    for (int i = threadIdx.x; i < S; i += NT) s.tmp[i] = s.y[i] + h0 * s.f[i];
+    __syncthreads();
+    rhs(n, c.kap, s.tmp, s.dy, s.r, s.part);
+    c.st.rhs_evals++;
+    for (int i = threadIdx.x; i < S; i += NT) s.tmp[i] = s.dy[i] - s.f[i];
+    __syncthreads();
+    const double d2 = wrms(s.tmp, s.wsc, 1.0, S, s.red) / h0;
+    const double dm = fmax(d1, d2);
+    const double h1 = dm <= 1e-15 ? fmax(1e-6, h0 * 1e-3) : sqrt(0.01 / dm);
+    double t = a.t0;
+    double h = fmin(fmin(100.0 * h0, h1), t_end - t);
+    for (int i = threadIdx.x; i < S; i += NT) {
+      D[i] = s.y[i];
+      D[S + i] = h * s.f[i];
+      for (int r = 2; r < kDiffRows; ++r) D[r * S + i] = 0.0;
+    }
+    jacobian(n, c.kap, s.y, c.g, c.Jv);
+    c.st.jac_evals++;
+    int q = 1, n_equal = 0;
+    bool jac_current = true, lu_valid = false;
+    double* slot = s.red + 40;
+    while (t < t_end) {
+      bool accepted = false;
+      double t_new = t, err = 0.0;
+      while (!accepted) {
+        if (c.st.attempts >= a.max_steps) {
+          status = CBX_CELL_MAX_STEPS;
+          break;
+        }
+        c.st.attempts++;
+        if (h < 10.0 * (::nextafter(t, __longlong_as_double(0x7ff0000000000000LL)) - t)) {
+          status = CBX_CELL_H_UNDERFLOW;
+          break;
+        }
+        t_new = t + h;
+        if (t_new > t_end) {
+          t_new = t_end;
+          rescale(D, S, q, (t_end - t) / h, s.Tm);
+          n_equal = 0;
+          lu_valid = false;
+          h = t_end - t;
+        }
+        const double gq = a.gam[q];
+        for (int i = threadIdx.x; i < S; i += NT) {
+          double yp = 0.0;
+          for (int j = 0; j <= q; ++j) yp += D[j * S + i];
+          double ps = 0.0;
+          for (int j = 1; j <= q; ++j) ps = fma(a.gam[j], D[j * S + i], ps);
+          s.yp[i] = yp;
+          s.psi[i] = ps / gq;
+          s.wsc[i] = 1.0 / (atol + rtol * fabs(yp));
+        }
+        __syncthreads();
+        const double cc = h / gq;
+        bool conv = false;
+        int iters = 0;
+        for (;;) {
+          if (!lu_valid) {
+            factor<LT>(c, cc);
+            lu_valid = true;
+          }
+          conv = newton<LT>(c, cc, &iters);
+          c.st.newton_iters += iters;
+          if (conv || jac_current) break;
+          jacobian(n, c.kap, s.yp, c.g, c.Jv);
+          c.st.jac_evals++;
+          jac_current = true;
+          lu_valid = false;
+        }
+        if (!conv) {
+          c.st.newton_fails++;
+          rescale(D, S, q, 0.5, s.Tm);
+          h *= 0.5;
+          n_equal = 0;
+          lu_valid = false;
+          continue;
+        }
+        for (int i = threadIdx.x; i < S; i += NT) s.wsc[i] = 1.0 / (atol + rtol * fabs(s.y[i]));
+        __syncthreads();
+        err = wrms(s.dv, s.wsc, 1.0 / (q + 1), S, s.red);
+        if (err > 1.0) {
+          c.st.error_fails++;
+          const double fac = fmax(0.2, 0.9 * uniform_pow(err, -1.0 / (q + 1), slot));
+          rescale(D, S, q, fac, s.Tm);
+          h *= fac;
+          n_equal = 0;
+          lu_valid = false;
+          continue;
+        }
+        accepted = true;
+      }
+      if (!accepted) break;
+      c.st.steps++;
+      t = t_new;
+      jac_current = false;
+      n_equal++;
+      for (int i = threadIdx.x; i < S; i += NT) {
+        const double d = s.dv[i];
+        D[(q + 2) * S + i] = d - D[(q + 1) * S + i];
+        D[(q + 1) * S + i] = d;
+        for (int j = q; j >= 0; --j) D[j * S + i] += D[(j + 1) * S + i];
+      }
+      __syncthreads();
+      if (n_equal < q + 1) continue;
+      const double em = q > 1 ? wrms(D + q * S, s.wsc, 1.0 / q, S, s.red) : INFINITY;
+      const double ep = q < kMaxOrder ? wrms(D + (q + 2) * S, s.wsc, 1.0 / (q + 2), S, s.red) : INFINITY;
+      double fc[3];
+      fc[0] = growth(em, q, slot);
+      fc[1] = growth(err, q + 1, slot);
+      fc[2] = growth(ep, q + 2, slot);
+      int best = 0;
+      if (fc[1] > fc[best]) best = 1;
+      if (fc[2] > fc[best]) best = 2;
+      q += best - 1;
+      const double fac = fmin(10.0, 0.9 * fc[best]);
+      rescale(D, S, q, fac, s.Tm);
+      h *= fac;
+      n_equal = 0;
+      lu_valid = false;
+    }
+    for (int i = threadIdx.x; i < S; i += NT) a.x_out[(size_t)__ldg(n.perm + i) * a.C + cell] = D[i];
+  }
+  if (threadIdx.x == 0) {
+    a.status[cell] = status;
+    if (a.stats) a.stats[cell] = c.st;
+  }
+  __syncthreads();
+}
+
+template <typename LT>
+__global__ void __launch_bounds__(NT, 1) solve_kernel(const SolveArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_cell;
+  Smem s;
+  layout(a.net.S, a.net.R, a.net.nseg, sizeof(LT) == 4, smem_raw, &s);
+  double* ws = a.ws + (size_t)blockIdx.x * a.ws_stride;
+  for (;;) {
+    if (threadIdx.x == 0) s_cell = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int cell = s_cell;
+    __syncthreads();
+    if (cell >= a.C) break;
+    solve_cell<LT>(a, cell, s, ws);
+  }
+}
+
+int launch_solver(const SolveArgs& a, bool mixed, int grid, void* stream) {
+  const size_t sm = smem_bytes(a.net.S, a.net.R, a.net.nseg, mixed);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  if (mixed) {
+    e = cudaFuncSetAttribute(solve_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    solve_kernel<float><<<grid, NT, sm, st>>>(a);
+  } else {
+    e = cudaFuncSetAttribute(solve_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    solve_kernel<double><<<grid, NT, sm, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+int solver_occupancy(int S, int R, int nseg, bool mixed) {
+  const size_t sm = smem_bytes(S, R, nseg, mixed);
+  if (S > 32 * kMaxColRegs || sm > device_smem_optin()) return 0;
+  int blocks = 0;
+  cudaError_t e;
+  if (mixed) {
+    e = cudaFuncSetAttribute(solve_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, solve_kernel<float>, NT, sm);
+  } else {
+    e = cudaFuncSetAttribute(solve_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, solve_kernel<double>, NT, sm);
+  }
+  return e == cudaSuccess ? blocks : 0;
+}
+
+int device_sm_count() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+  return v;
+}
+
+size_t device_smem_optin() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return (size_t)v;
+}
+
+}  // namespace cbx

@@ -1,0 +1,135 @@
+"""CUDA path vs the CPU oracle, element by element (GPU).
+
+Twin parity: the GPU runs the same BDF algorithm with the same constants as
+the oracle, so abundances above 1e-12 per n_H must agree within 1e-4
+relative. Conservation of the five elements and of charge is checked on every
+cell at 1e-10 relative (charge relative to sum |q_i| x_i(0)).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import bdf, chem  # noqa: E402
+from paper_2511_10558_gb300 import build as _build  # noqa: E402
+
+_build.build()
+from paper_2511_10558_gb300 import carbox, synth  # noqa: E402
+
+YR = synth.YEAR
+TOL = 1e-4
+FLOOR = 1e-12
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def gpu_solve(N, phi, x0, t_end, dev, **kw):
+    phi_d = torch.tensor(np.asarray(phi), dtype=torch.float64, device=dev).contiguous()
+    x0_d = torch.tensor(np.asarray(x0), dtype=torch.float64, device=dev).contiguous()
+    stats = torch.zeros((phi_d.shape[0], 10), dtype=torch.int32, device=dev)
+    x, st, stats = carbox.solve(N, phi_d, x0_d, 0.0, t_end, carbox.options(**kw), stats=stats)
+    torch.cuda.synchronize()
+    return x.cpu().numpy(), st.cpu().numpy(), stats.cpu().numpy()
+
+
+def assert_twin(x_gpu, x_ref, what):
+    big = x_ref > FLOOR
+    rel = np.abs(x_gpu[big] / x_ref[big] - 1)
+    assert rel.max() <= TOL, f"{what}: max rel diff {rel.max():.3e} at species {np.flatnonzero(big)[rel.argmax()]}"
+
+
+def assert_conserved(net, x0, x):
+    E0, Q0 = chem.element_totals(net, x0)
+    E1, Q1 = chem.element_totals(net, x)
+    assert np.all(np.abs(E1 - E0) <= 1e-10 * E0), (E1 - E0) / E0
+    assert abs(Q1 - Q0) <= 1e-10 * (np.abs(net.charge) @ x0)
+
+
+@pytest.mark.parametrize("prec", [carbox.CBX_FP64, carbox.CBX_MIXED])
+def test_single_cell_32(dev, net32, prec):
+    phi = synth.one_cell()
+    x0 = synth.initial_abundances(net32)
+    t_end = 1e6 * YR
+    ref = bdf.solve_cell(net32, phi[0], x0, 0.0, t_end, 1e-4, 1e-20)
+    N = carbox.Network.from_synth(net32)
+    x, st, stats = gpu_solve(N, phi, x0[:, None], t_end, dev, precision=prec)
+    assert st[0] == carbox.CBX_CELL_OK
+    assert_twin(x[:, 0], ref.x, "32-species cell")
+    assert_conserved(net32, x0, x[:, 0])
+    s = dict(zip(carbox.STATS_FIELDS, stats[0]))
+    print("gpu", s, "\noracle", ref.stats)
+    assert abs(s["steps"] - ref.stats["steps"]) <= 0.02 * ref.stats["steps"]
+
+
+@pytest.mark.parametrize("prec", [carbox.CBX_FP64, carbox.CBX_MIXED])
+def test_batch_150_sampled(dev, net150, prec):
+    C = 300  # several waves of CTAs and a ragged last wave
+    phi = synth.cells(C)
+    x0 = np.repeat(synth.initial_abundances(net150)[:, None], C, axis=1)
+    t_end = 1e6 * YR
+    N = carbox.Network.from_synth(net150)
+    x, st, stats = gpu_solve(N, phi, x0, t_end, dev, precision=prec)
+    assert np.all(st == carbox.CBX_CELL_OK)
+    for c in range(C):
+        assert_conserved(net150, x0[:, c], x[:, c])
+    for c in [0, 1, 2, 77, 150, C - 1]:
+        ref = bdf.solve_cell(net150, phi[c], x0[:, c], 0.0, t_end, 1e-4, 1e-20)
+        assert_twin(x[:, c], ref.x, f"cell {c}")
+
+
+def test_cell_independent_of_batch(dev, net150):
+    # a cell's result is bitwise the same alone and inside a batch
+    phi = synth.cells(40)
+    x0 = np.repeat(synth.initial_abundances(net150)[:, None], 40, axis=1)
+    N = carbox.Network.from_synth(net150)
+    xb, _, _ = gpu_solve(N, phi, x0, 1e5 * YR, dev)
+    xa, _, _ = gpu_solve(N, phi[17:18], x0[:, 17:18], 1e5 * YR, dev)
+    np.testing.assert_array_equal(xa[:, 0], xb[:, 17])
+
+
+def test_edge_cases(dev, net32):
+    N = carbox.Network.from_synth(net32)
+    x0 = synth.initial_abundances(net32)
+    # empty batch is a no-op
+    phi0 = torch.zeros((0, 5), dtype=torch.float64, device=dev)
+    x00 = torch.zeros((net32.n_species, 0), dtype=torch.float64, device=dev)
+    carbox.solve(N, phi0, x00, 0.0, 1.0)
+    # t_end == t0 returns the input; bad parameters give BAD_INPUT without touching the others
+    phi = np.repeat(synth.one_cell(), 3, axis=0)
+    phi[1, 1] = 0.0       # T = 0
+    phi[2, 0] = np.nan    # n_H = NaN
+    xs = np.repeat(x0[:, None], 3, axis=1)
+    x, st, _ = gpu_solve(N, phi, xs, 1e4 * YR, dev)
+    assert list(st) == [carbox.CBX_CELL_OK, carbox.CBX_CELL_BAD_INPUT, carbox.CBX_CELL_BAD_INPUT]
+    np.testing.assert_array_equal(x[:, 1], x0)
+    # a step budget that is too small ends with MAX_STEPS
+    x, st, stats = gpu_solve(N, phi[:1], xs[:, :1], 1e6 * YR, dev, max_steps=20)
+    assert st[0] == carbox.CBX_CELL_MAX_STEPS and stats[0, 1] == 20
+
+
+def test_argument_errors(dev, net32):
+    N = carbox.Network.from_synth(net32)
+    phi = torch.tensor(synth.one_cell(), device=dev)
+    x0 = torch.tensor(synth.initial_abundances(net32)[:, None], device=dev).contiguous()
+    with pytest.raises(carbox.CarboxError):
+        carbox.solve(N, phi, x0, 1.0, 0.0)                      # t_end < t0
+    with pytest.raises(carbox.CarboxError):
+        carbox.solve(N, phi, x0, 0.0, 1.0, carbox.options(rtol=0.0))
+    with pytest.raises(carbox.CarboxError):
+        carbox.solve(N, phi, x0, 0.0, 1.0, carbox.options(precision=7))
+
+
+def test_host_buffers_match_device(dev, net150):
+    phi = synth.cells(20)
+    x0 = np.repeat(synth.initial_abundances(net150)[:, None], 20, axis=1)
+    N = carbox.Network.from_synth(net150)
+    xd, sd, _ = gpu_solve(N, phi, x0, 1e5 * YR, dev)
+    xh, sh, _ = carbox.solve_host(N, phi, x0, 0.0, 1e5 * YR)
+    np.testing.assert_array_equal(xd, xh)
+    np.testing.assert_array_equal(sd, sh)
