@@ -115,6 +115,8 @@ typedef struct {
   int newton_iters;   /* Newton iterations */
   int refine_sweeps;  /* refinement sweeps (CBX_MIXED) */
   int reserved;
+  long long t_begin_ns; /* device global timer when the cell's CTA started it */
+  long long t_end_ns;   /* device global timer when the cell retired */
 } cbx_cell_stats;
 
 typedef struct {

@@ -31,6 +31,16 @@ def _deps():
     return files
 
 
+def source_hash() -> str:
+    """Hash of the kernel sources (identifies the build a profile was taken on)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(SOURCES) + ["internal.h"]:
+        h.update(open(os.path.join(CSRC, f), "rb").read())
+    h.update(open(os.path.join(INCLUDE, "carbox.h"), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and os.path.exists(LIB):
         newest = max(os.path.getmtime(f) for f in _deps())

@@ -42,10 +42,29 @@ class cbx_options(C.Structure):
 
 class cbx_cell_stats(C.Structure):
     _fields_ = [(n, C.c_int) for n in ("steps", "attempts", "error_fails", "newton_fails", "rhs_evals",
-                                        "jac_evals", "lu_factors", "newton_iters", "refine_sweeps", "reserved")]
+                                        "jac_evals", "lu_factors", "newton_iters", "refine_sweeps", "reserved")] + \
+        [("t_begin_ns", C.c_longlong), ("t_end_ns", C.c_longlong)]
 
 
-STATS_FIELDS = [f for f, _ in cbx_cell_stats._fields_ if f != "reserved"]
+STATS_FIELDS = ["steps", "attempts", "error_fails", "newton_fails", "rhs_evals", "jac_evals", "lu_factors",
+                "newton_iters", "refine_sweeps"]
+STATS_INTS = 14  # int32 words per cbx_cell_stats (10 ints + 2 int64)
+
+
+def stats_tensor(n_cells, device):
+    """A zeroed device buffer for per-cell cbx_cell_stats, as int32 [C, 14]."""
+    import torch
+    return torch.zeros((n_cells, STATS_INTS), dtype=torch.int32, device=device)
+
+
+def stats_dict(arr):
+    """Decode int32 [C, 14] stats rows into a dict of numpy arrays."""
+    arr = np.ascontiguousarray(arr, dtype=np.int32)
+    out = {f: arr[:, i] for i, f in enumerate(STATS_FIELDS)}
+    t = arr[:, 10:14].copy().view(np.int64)
+    out["t_begin_ns"] = t[:, 0]
+    out["t_end_ns"] = t[:, 1]
+    return out
 
 
 class cbx_netinfo(C.Structure):
@@ -150,13 +169,20 @@ def _ptr(t):
 def solve(net, phi, x0, t0, t_end, opt=None, stream=None, x_out=None, status=None, stats=None):
     """cbx_solve on torch CUDA tensors: phi [C, 5] f64, x0 [S, C] f64 (contiguous).
 
-    Returns (x_out [S, C], status [C] int32, stats [C, 10] int32 or None).
+    Returns (x_out [S, C], status [C] int32, stats [C, 14] int32 or None; see stats_dict).
     """
     import torch
     Cn = phi.shape[0]
     assert phi.is_cuda and phi.dtype == torch.float64 and phi.is_contiguous() and phi.shape[1] == 5
     assert x0.is_cuda and x0.dtype == torch.float64 and x0.is_contiguous() and tuple(x0.shape) == (net.S, Cn)
     dev = phi.device
+    if stats is not None:
+        assert (stats.is_cuda and stats.dtype == torch.int32 and stats.is_contiguous()
+                and tuple(stats.shape) == (Cn, STATS_INTS)), "stats must be stats_tensor(C, device)"
+    if x_out is not None:
+        assert x_out.is_cuda and x_out.dtype == torch.float64 and x_out.is_contiguous() and tuple(x_out.shape) == (net.S, Cn)
+    if status is not None:
+        assert status.is_cuda and status.dtype == torch.int32 and status.is_contiguous() and tuple(status.shape) == (Cn,)
     if x_out is None:
         x_out = torch.empty((net.S, Cn), dtype=torch.float64, device=dev)
     if status is None:
@@ -177,7 +203,7 @@ def solve_host(net, phi, x0, t0, t_end, opt=None, stream=None, want_stats=False)
     assert x0.shape == (net.S, Cn)
     x_out = np.empty((net.S, Cn))
     status = np.empty(Cn, dtype=np.int32)
-    stats = np.zeros((Cn, 10), dtype=np.int32) if want_stats else None
+    stats = np.zeros((Cn, STATS_INTS), dtype=np.int32) if want_stats else None
     o = opt if opt is not None else options()
     s = C.c_void_p(stream.cuda_stream) if stream is not None else None
     check(lib.cbx_solve_host(net.handle, phi.ctypes.data_as(C.c_void_p), x0.ctypes.data_as(C.c_void_p), Cn,

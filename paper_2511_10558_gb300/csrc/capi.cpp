@@ -86,6 +86,7 @@ int upload(cbx_network* n) {
   d.R = h.R;
   d.nnzJ = h.nnzJ;
   d.nseg = h.nseg;
+  d.kdense = h.kdense;
   d.rtype = (const int*)(b + o_rtype);
   d.alpha = (const double*)(b + o_alpha);
   d.beta = (const double*)(b + o_beta);

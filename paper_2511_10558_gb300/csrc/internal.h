@@ -18,6 +18,7 @@ constexpr int kSegLen = 16;            // entries per right-hand-side gather seg
 // (fill-reducing order); perm maps internal -> user index.
 struct DevNet {
   int S, R, nnzJ, nseg;
+  int kdense;            // pivots k >= kdense have a fully dense trailing block
   const int* rtype;      // [R]
   const double* alpha;   // [R]
   const double* beta;    // [R]
@@ -41,7 +42,7 @@ struct DevNet {
 
 // Host-side compiled network.
 struct HostNet {
-  int S = 0, R = 0, nnzJ = 0, nnzLU = 0, nseg = 0;
+  int S = 0, R = 0, nnzJ = 0, nnzLU = 0, nseg = 0, kdense = 0;
   double lu_flops = 0;
   std::vector<int> perm, iperm;
   std::vector<int> rtype, ra, rb;

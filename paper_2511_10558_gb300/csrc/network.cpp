@@ -209,6 +209,13 @@ std::string compile_network(const cbx_species* sp, int S, const cbx_reaction* rx
   }
   n.nnzLU = 0;
   for (uint8_t v : F) n.nnzLU += v;
+  // first pivot from which every L column and U row is the full range k+1..S-1
+  n.kdense = S;
+  for (int k = S - 1; k >= 0; --k) {
+    const int nl = n.piv_lptr[k + 1] - n.piv_lptr[k], nu = n.piv_uptr[k + 1] - n.piv_uptr[k];
+    if (nl != S - k - 1 || nu != S - k - 1) break;
+    n.kdense = k;
+  }
   n.lu_flops = flops;
   return "";
 }

@@ -47,6 +47,12 @@ constexpr unsigned FULL = 0xffffffffu;
 
 // ---------------------------------------------------------------- helpers
 
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
 // Deterministic block sum: warp trees, then the NW partials in a fixed order.
 // Every thread returns the same value. Contains two barriers.
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -169,109 +175,480 @@ __device__ void jacobian(const DevNet& n, const double* __restrict__ kap, const 
 
 // ---------------------------------------------------------------- linear algebra
 
+__host__ __device__ inline int lead_dim(int S) { return S | 1; }  // odd: conflict-free column access
+
 template <typename LT>
 __device__ void build_matrix(const DevNet& n, const double* Jv, double c, LT* M) {
-  const int S = n.S;
-  for (int idx = threadIdx.x; idx < S * S; idx += NT) M[idx] = LT(0);
+  const int S = n.S, ld = lead_dim(S);
+  for (int idx = threadIdx.x; idx < S * ld; idx += NT) M[idx] = LT(0);
   __syncthreads();
   for (int s = threadIdx.x; s < n.nnzJ; s += NT) {
     const int i = n.jrow[s], l = n.jcol[s];
     const double cj = c * Jv[s];
-    M[i * S + l] = (LT)(i == l ? 1.0 - cj : -cj);
+    M[i * ld + l] = (LT)(i == l ? 1.0 - cj : -cj);
   }
   __syncthreads();
 }
 
-// In-place LU without pivoting on the static fill pattern: per pivot k, one
-// warp scales the L column by the reciprocal pivot; then warps take the rows
-// of L(:,k), lanes the columns of U(k,:) held in registers.
-template <typename LT>
-__device__ void lu_factor(const DevNet& n, LT* M, LT* invd) {
-  const int S = n.S;
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int k = 0; k < S; ++k) {
-    const int l0 = __ldg(n.piv_lptr + k), l1 = __ldg(n.piv_lptr + k + 1);
-    if (w == 0) {
-      const LT inv = LT(1) / M[k * S + k];
-      if (lane == 0) invd[k] = inv;
-      for (int e = l0 + lane; e < l1; e += 32) {
-        const int i = __ldg(n.piv_l + e);
-        M[i * S + k] *= inv;
-      }
-    }
-    __syncthreads();
-    const int u0 = __ldg(n.piv_uptr + k), nu = __ldg(n.piv_uptr + k + 1) - u0;
-    if (l1 > l0 && nu > 0) {
-      int jc[kMaxColRegs];
-      LT uv[kMaxColRegs];
-#pragma unroll
-      for (int m = 0; m < kMaxColRegs; ++m) {
-        const int b = lane + 32 * m;
-        jc[m] = b < nu ? __ldg(n.piv_u + u0 + b) : 0;
-        uv[m] = b < nu ? M[k * S + jc[m]] : LT(0);
-      }
-      for (int e = l0 + w; e < l1; e += NW) {
-        const int i = __ldg(n.piv_l + e);
-        LT* row = M + i * S;
-        const LT l = row[k];
-#pragma unroll
-        for (int m = 0; m < kMaxColRegs; ++m) {
-          if (lane + 32 * m < nu) row[jc[m]] -= l * uv[m];
-        }
-      }
-    }
-    __syncthreads();
+// ---------------------------------------------------------------- FP64 LU (Crout form)
+//
+// M = L U with L lower triangular (its diagonal holds the pivots) and U unit
+// upper triangular, in place, without pivoting, on the static fill pattern.
+// Row k of U is stored pre-scaled by 1/pivot_k, so every warp applies the
+// rank-1 update a_ij -= a_ik u_kj (rows i of L(:,k), columns j of U(k,:)) with
+// no separate scaling phase: one barrier per pivot. Warp 0 updates row k+1
+// first and then prepares pivot k+1 (reciprocal pivot, row scaling) while the
+// other warps work on their rows. Pivots k >= kd have a fully dense trailing
+// block and use index ranges instead of the per-pivot lists.
+
+__device__ __forceinline__ int lrow(const DevNet& n, bool dense, int k, int e) {
+  return dense ? k + 1 + e : __ldg(n.piv_l + e);
+}
+
+// Reciprocal pivot and scaling of row k of U (warp-wide call).
+__device__ void prep_pivot(const DevNet& n, double* M, double* invd, int k, int kd, int lane) {
+  const int S = n.S, ld = lead_dim(S);
+  const double inv = __drcp_rn(M[k * ld + k]);  // correctly rounded: equals 1.0 / pivot
+  if (lane == 0) invd[k] = inv;
+  if (k >= kd) {
+    for (int j = k + 1 + lane; j < S; j += 32) M[k * ld + j] *= inv;
+  } else {
+    const int u1 = __ldg(n.piv_uptr + k + 1);
+    for (int e = __ldg(n.piv_uptr + k) + lane; e < u1; e += 32) M[k * ld + __ldg(n.piv_u + e)] *= inv;
   }
 }
 
-// v <- L^{-1} v (unit lower), blocks of 32: one warp solves the diagonal block
-// with shuffles, then every thread updates one row below it.
-template <typename LT>
-__device__ void forward_solve(const LT* M, int S, LT* v) {
+// All rows of L(:,k) assigned to this warp, with exactly MC column groups of
+// U(k,:) per lane (a predicated FP64 instruction still takes the FP64 pipe).
+template <int MC>
+__device__ __forceinline__ void crout_rows(const DevNet& n, double* M, double* invd, int k, int kd, bool dense,
+                                           int l0, int l1, int u0, int nu, bool next_in_l) {
+  const int ld = lead_dim(n.S);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int jc[MC];
+  double uv[MC];
+#pragma unroll
+  for (int m = 0; m < MC; ++m) {
+    const int b = lane + 32 * m;
+    jc[m] = 0;
+    uv[m] = 0.0;
+    if (b < nu) {
+      jc[m] = dense ? k + 1 + b : __ldg(n.piv_u + u0 + b);
+      uv[m] = M[k * ld + jc[m]];
+    }
+  }
+  // warp 0 takes row k+1 alone when it is in L(:,k) (then prepares pivot
+  // k+1); the other rows go to warps 1..NW-1, two at a time
+  const int first = next_in_l ? l0 + 1 : l0;
+  const int nw = next_in_l ? NW - 1 : NW;
+  const int wi = next_in_l ? w - 1 : w;
+  const bool row_next = next_in_l && w == 0;
+  for (int e = row_next ? l0 : first + wi; row_next ? e == l0 : e < l1; e += row_next ? 1 : 2 * nw) {
+    const bool two = !row_next && e + nw < l1;
+    double* r0 = M + lrow(n, dense, k, e) * ld;
+    double* r1 = two ? M + lrow(n, dense, k, e + nw) * ld : r0;
+    const double a = r0[k], b = r1[k];
+    double x0[MC], x1[MC];
+#pragma unroll
+    for (int m = 0; m < MC; ++m) {
+      x0[m] = r0[jc[m]];
+      x1[m] = r1[jc[m]];
+    }
+#pragma unroll
+    for (int m = 0; m < MC; ++m) x0[m] = fma(-a, uv[m], x0[m]);
+    if (two) {
+#pragma unroll
+      for (int m = 0; m < MC; ++m) x1[m] = fma(-b, uv[m], x1[m]);
+    }
+#pragma unroll
+    for (int m = 0; m < MC; ++m) {
+      if (lane + 32 * m < nu) {
+        r0[jc[m]] = x0[m];
+        if (two) r1[jc[m]] = x1[m];
+      }
+    }
+    if (row_next) {
+      __syncwarp();
+      prep_pivot(n, M, invd, k + 1, kd, lane);
+    }
+  }
+}
+
+__device__ void lu_crout64(const DevNet& n, double* M, double* invd) {
+  const int S = n.S, ld = lead_dim(S), kd = n.kdense;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (w == 0) prep_pivot(n, M, invd, 0, kd, lane);
+  __syncthreads();
+  for (int k = 0; k + 1 < S; ++k) {
+    const bool dense = k >= kd;
+    int l0, l1, u0, nu;
+    if (dense) {
+      l0 = 0;
+      l1 = S - k - 1;
+      u0 = 0;
+      nu = S - k - 1;
+    } else {
+      l0 = __ldg(n.piv_lptr + k);
+      l1 = __ldg(n.piv_lptr + k + 1);
+      u0 = __ldg(n.piv_uptr + k);
+      nu = __ldg(n.piv_uptr + k + 1) - u0;
+    }
+    const bool next_in_l = l1 > l0 && lrow(n, dense, k, l0) == k + 1;
+    if (w == 0 && !next_in_l) prep_pivot(n, M, invd, k + 1, kd, lane);
+    if (nu > 0) {
+      switch ((nu + 31) >> 5) {
+        case 1: crout_rows<1>(n, M, invd, k, kd, dense, l0, l1, u0, nu, next_in_l); break;
+        case 2: crout_rows<2>(n, M, invd, k, kd, dense, l0, l1, u0, nu, next_in_l); break;
+        case 3: crout_rows<3>(n, M, invd, k, kd, dense, l0, l1, u0, nu, next_in_l); break;
+        case 4: crout_rows<4>(n, M, invd, k, kd, dense, l0, l1, u0, nu, next_in_l); break;
+        case 5: crout_rows<5>(n, M, invd, k, kd, dense, l0, l1, u0, nu, next_in_l); break;
+        case 6: crout_rows<6>(n, M, invd, k, kd, dense, l0, l1, u0, nu, next_in_l); break;
+        case 7: crout_rows<7>(n, M, invd, k, kd, dense, l0, l1, u0, nu, next_in_l); break;
+        default: crout_rows<8>(n, M, invd, k, kd, dense, l0, l1, u0, nu, next_in_l); break;
+      }
+    } else if (w == 0 && next_in_l) {
+      prep_pivot(n, M, invd, k + 1, kd, lane);
+    }
+    __syncthreads();
+  }
+  // L(:,k) /= pivot_k: M now holds L (unit lower), the pivots in invd (as
+  // reciprocals) and U (unit upper), so both triangular solves are unit.
+  for (int i = 1 + (threadIdx.x >> 5); i < S; i += NW)
+    for (int k = lane; k < i; k += 32) M[i * ld + k] *= invd[k];
+  __syncthreads();
+}
+
+// v <- D^{-1} L^{-1} v (L unit lower, D the pivots with reciprocals in invd),
+// blocks of 32: one warp solves the diagonal block with shuffles, then one
+// thread per row applies the block to the rows below (four partial sums to
+// shorten the FP64 dependency chain); D^{-1} last, element-wise.
+__device__ void forward_crout64(const double* M, const double* invd, int S, double* v) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, ld = lead_dim(S);
   for (int kb = 0; kb < S; kb += 32) {
     const int nb = min(32, S - kb);
     if (w == 0) {
-      LT val = lane < nb ? v[kb + lane] : LT(0);
-      for (int k = 0; k < nb - 1; ++k) {
-        const LT yk = __shfl_sync(FULL, val, k);
-        if (lane > k && lane < nb) val -= M[(kb + lane) * S + kb + k] * yk;
+      double val = lane < nb ? v[kb + lane] : 0.0;
+      const double* row = M + (kb + min(lane, nb - 1)) * ld + kb;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        if (c < nb) {
+          const double yc = __shfl_sync(FULL, val, c);
+          if (lane > c && lane < nb) val = fma(-row[c], yc, val);
+        }
       }
       if (lane < nb) v[kb + lane] = val;
     }
     __syncthreads();
     for (int i = kb + nb + threadIdx.x; i < S; i += NT) {
-      LT acc = v[i];
-      const LT* row = M + i * S + kb;
-      for (int k = 0; k < nb; ++k) acc -= row[k] * v[kb + k];
-      v[i] = acc;
+      const double* row = M + i * ld + kb;
+      double p0 = v[i], p1 = 0.0, p2 = 0.0, p3 = 0.0;
+      int c = 0;
+      for (; c + 4 <= nb; c += 4) {
+        p0 = fma(-row[c], v[kb + c], p0);
+        p1 = fma(-row[c + 1], v[kb + c + 1], p1);
+        p2 = fma(-row[c + 2], v[kb + c + 2], p2);
+        p3 = fma(-row[c + 3], v[kb + c + 3], p3);
+      }
+      for (; c < nb; ++c) p0 = fma(-row[c], v[kb + c], p0);
+      v[i] = (p0 + p1) + (p2 + p3);
     }
     __syncthreads();
   }
+  for (int i = threadIdx.x; i < S; i += NT) v[i] *= invd[i];
+  __syncthreads();
 }
 
-// v <- U^{-1} v (upper, reciprocal diagonal in invd), blocks from the bottom.
-template <typename LT>
-__device__ void backward_solve(const LT* M, const LT* invd, int S, LT* v) {
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int ke = S; ke > 0; ke -= 32) {
-    const int kb = max(0, ke - 32), nb = ke - kb;
+// v <- U^{-1} v for the unit upper Crout factor, blocks of 32 from the bottom.
+__device__ void backward_crout64(const double* M, int S, double* v) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, ld = lead_dim(S);
+  for (int kb = ((S - 1) / 32) * 32; kb >= 0; kb -= 32) {
+    const int nb = min(32, S - kb);
     if (w == 0) {
-      LT val = lane < nb ? v[kb + lane] : LT(0);
-      for (int k = nb - 1; k >= 0; --k) {
-        if (lane == k) val *= invd[kb + k];
-        const LT xk = __shfl_sync(FULL, val, k);
-        if (lane < k) val -= M[(kb + lane) * S + kb + k] * xk;
+      double val = lane < nb ? v[kb + lane] : 0.0;
+      const double* row = M + (kb + min(lane, nb - 1)) * ld + kb;
+#pragma unroll
+      for (int c = 31; c >= 0; --c) {
+        if (c < nb) {
+          const double xc = __shfl_sync(FULL, val, c);
+          if (lane < c) val = fma(-row[c], xc, val);
+        }
       }
       if (lane < nb) v[kb + lane] = val;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kb; i += NT) {
-      LT acc = v[i];
-      const LT* row = M + i * S + kb;
-      for (int k = 0; k < nb; ++k) acc -= row[k] * v[kb + k];
-      v[i] = acc;
+      const double* row = M + i * ld + kb;
+      double p0 = v[i], p1 = 0.0, p2 = 0.0, p3 = 0.0;
+      int c = 0;
+      for (; c + 4 <= nb; c += 4) {
+        p0 = fma(-row[c], v[kb + c], p0);
+        p1 = fma(-row[c + 1], v[kb + c + 1], p1);
+        p2 = fma(-row[c + 2], v[kb + c + 2], p2);
+        p3 = fma(-row[c + 3], v[kb + c + 3], p3);
+      }
+      for (; c < nb; ++c) p0 = fma(-row[c], v[kb + c], p0);
+      v[i] = (p0 + p1) + (p2 + p3);
     }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- blocked LU (FP32 path)
+
+constexpr int NB = 32;  // panel width
+
+// Right-looking blocked LU without pivoting, panel width NB, on a dense
+// row-major matrix (leading dimension ld). Per panel: (1) the panel columns are
+// factored with one barrier per column, each thread keeping one row of the
+// panel in registers (the column loop is unrolled at compile time, so register
+// indices and bounds are static); (2) thread-per-column forward substitution
+// forms U12 = L11^{-1} A12 in registers and, on NB appended identity columns,
+// L11^{-1}, which then replaces L11 in place for the block forward solves;
+// (3) register-tiled update A22 -= L21 U12. After the last panel the upper
+// diagonal blocks are replaced by U_bb^{-1} (strict upper part; the diagonal
+// reciprocals stay in invd).
+
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
+template <typename LT, bool FULL>
+__device__ __forceinline__ void panel_factor(LT* M, LT* invd, int S, int ld, int kb, int nb) {
+  const int tid = threadIdx.x;
+  const int i = kb + tid;
+  const bool own = i < S;
+  LT r[NB];
+#pragma unroll
+  for (int jj = 0; jj < NB; ++jj) r[jj] = own && (FULL || jj < nb) ? M[i * ld + kb + jj] : LT(0);
+#pragma unroll
+  for (int c = 0; c < NB; ++c) {
+    if (FULL || c < nb) {
+      const int k = kb + c;
+      if (i == k) {
+#pragma unroll
+        for (int jj = c; jj < NB; ++jj)
+          if (FULL || jj < nb) M[k * ld + kb + jj] = r[jj];
+      }
+      __syncthreads();
+      const LT* prow = M + k * ld + kb;
+      if (own && i > k) {
+        const LT l = r[c] * recip(prow[c]);
+        r[c] = l;
+#pragma unroll
+        for (int jj = c + 1; jj < NB; ++jj)
+          if (FULL || jj < nb) r[jj] -= l * prow[jj];
+      }
+      if (tid == 0) invd[k] = recip(prow[c]);
+    }
+  }
+  __syncthreads();
+  if (own && i >= kb + nb) {
+#pragma unroll
+    for (int jj = 0; jj < NB; ++jj)
+      if (FULL || jj < nb) M[i * ld + kb + jj] = r[jj];
+  } else if (own) {
+#pragma unroll
+    for (int jj = 0; jj < NB; ++jj)
+      if (kb + jj < i) M[i * ld + kb + jj] = r[jj];
+  }
+  __syncthreads();
+}
+
+template <typename LT, bool FULL>
+__device__ __forceinline__ void panel_u12(LT* M, int S, int ld, int kb, int nb) {
+  const int ke = kb + nb, ncol = S - ke, t = threadIdx.x;
+  const bool a12 = t < ncol, ident = !a12 && t < ncol + nb;
+  const int col = ke + t, jj = t - ncol;
+  LT v[NB];
+#pragma unroll
+  for (int r = 0; r < NB; ++r) v[r] = a12 && (FULL || r < nb) ? M[(kb + r) * ld + col] : (ident && r == jj ? LT(1) : LT(0));
+  if (a12 || ident) {
+    const LT* L = M + kb * ld + kb;
+#pragma unroll
+    for (int c = 0; c < NB - 1; ++c) {
+#pragma unroll
+      for (int r = c + 1; r < NB; ++r)
+        if (FULL || r < nb) v[r] -= L[r * ld + c] * v[c];
+    }
+  }
+  __syncthreads();
+  if (a12) {
+#pragma unroll
+    for (int r = 0; r < NB; ++r)
+      if (FULL || r < nb) M[(kb + r) * ld + col] = v[r];
+  } else if (ident) {
+#pragma unroll
+    for (int r = 0; r < NB; ++r)
+      if (r > jj && (FULL || r < nb)) M[(kb + r) * ld + kb + jj] = v[r];
+  }
+  __syncthreads();
+}
+
+// A22 -= L21 U12 over rows/cols [ke, S): warps take 4-row strips, lanes the
+// columns ke + lane + 32 g (exactly NG groups); the inner dimension is nb.
+template <typename LT, int NG>
+__device__ __forceinline__ void trailing_update_ng(LT* M, int S, int ld, int kb, int nb) {
+  const int ke = kb + nb, ncol = S - ke;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  bool colok[NG];
+#pragma unroll
+  for (int g = 0; g < NG; ++g) colok[g] = lane + 32 * g < ncol;
+  for (int rs = warp; rs * 4 < ncol; rs += NW) {
+    const int i0 = ke + rs * 4;
+    LT acc[4][NG];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int g = 0; g < NG; ++g) acc[r][g] = LT(0);
+    const LT* lp[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) lp[r] = M + min(i0 + r, S - 1) * ld + kb;
+    const LT* up = M + kb * ld + ke + lane;
+    for (int c = 0; c < nb; ++c) {
+      LT lv[4], uu[NG];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) lv[r] = lp[r][c];
+#pragma unroll
+      for (int g = 0; g < NG; ++g) uu[g] = colok[g] ? up[32 * g] : LT(0);
+#pragma unroll
+      for (int g = 0; g < NG; ++g)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[r][g] += lv[r] * uu[g];
+      up += ld;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      if (i0 + r < S) {
+        LT* row = M + (i0 + r) * ld + ke + lane;
+#pragma unroll
+        for (int g = 0; g < NG; ++g)
+          if (colok[g]) row[32 * g] -= acc[r][g];
+      }
+    }
+  }
+}
+
+template <typename LT>
+__device__ __forceinline__ void trailing_update(LT* M, int S, int ld, int kb, int nb) {
+  const int ncol = S - kb - nb;
+  if (ncol <= 0) return;
+  switch ((ncol + 31) >> 5) {
+    case 1: trailing_update_ng<LT, 1>(M, S, ld, kb, nb); break;
+    case 2: trailing_update_ng<LT, 2>(M, S, ld, kb, nb); break;
+    case 3: trailing_update_ng<LT, 3>(M, S, ld, kb, nb); break;
+    case 4: trailing_update_ng<LT, 4>(M, S, ld, kb, nb); break;
+    case 5: trailing_update_ng<LT, 5>(M, S, ld, kb, nb); break;
+    case 6: trailing_update_ng<LT, 6>(M, S, ld, kb, nb); break;
+    case 7: trailing_update_ng<LT, 7>(M, S, ld, kb, nb); break;
+    default: trailing_update_ng<LT, 8>(M, S, ld, kb, nb); break;
+  }
+  __syncthreads();
+}
+
+template <typename LT>
+__device__ void lu_blocked(LT* M, LT* invd, int S, int ld) {
+  for (int kb = 0; kb < S; kb += NB) {
+    const int nb = min(NB, S - kb);
+    if (nb == NB) {
+      panel_factor<LT, true>(M, invd, S, ld, kb, nb);
+      panel_u12<LT, true>(M, S, ld, kb, nb);
+    } else {
+      panel_factor<LT, false>(M, invd, S, ld, kb, nb);
+      panel_u12<LT, false>(M, S, ld, kb, nb);
+    }
+    trailing_update<LT>(M, S, ld, kb, nb);
+  }
+  // U_bb^{-1}: thread per column of each diagonal block, all blocks at once
+  {
+    const int tid = threadIdx.x;
+    const int nblk = (S + NB - 1) / NB;
+    const int b = tid / NB, jj = tid % NB;
+    LT x[NB];
+    const bool act = b < nblk && b * NB + jj < S;
+    const int kb = b * NB;
+    if (act) {
+      const LT* U = M + kb * ld + kb;
+#pragma unroll
+      for (int r = NB - 1; r >= 0; --r) {
+        LT acc = r == jj ? LT(1) : LT(0);
+#pragma unroll
+        for (int c = r + 1; c < NB; ++c)
+          if (c <= jj) acc -= U[r * ld + c] * x[c];
+        x[r] = r <= jj ? acc * invd[kb + r] : LT(0);
+      }
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+      for (int r = 0; r < NB; ++r)
+        if (r < jj) M[(kb + r) * ld + kb + jj] = x[r];
+    }
+    __syncthreads();
+  }
+}
+
+// v <- (L U)^{-1} v with the blocked factors: per diagonal block one
+// lower-triangular mat-vec by L_bb^{-1}, then a rectangular update of the rows
+// below; backwards the same with U_bb^{-1} (diagonal via invd) and the rows above.
+template <typename LT, bool FULL>
+__device__ __forceinline__ void rows_minus_block(const LT* M, int ld, const LT* vb, int nb, LT* v, int i0, int i1) {
+  // v[i] -= sum_c M[i][c] vb[c] for rows i in [i0, i1); M points at column kb
+  for (int i = i0 + threadIdx.x; i < i1; i += NT) {
+    const LT* row = M + i * ld;
+    LT p0 = v[i], p1 = LT(0), p2 = LT(0), p3 = LT(0);
+#pragma unroll
+    for (int c = 0; c < NB; c += 4) {
+      if (FULL || c < nb) p0 -= row[c] * vb[c];
+      if (FULL || c + 1 < nb) p1 -= row[c + 1] * vb[c + 1];
+      if (FULL || c + 2 < nb) p2 -= row[c + 2] * vb[c + 2];
+      if (FULL || c + 3 < nb) p3 -= row[c + 3] * vb[c + 3];
+    }
+    v[i] = (p0 + p1) + (p2 + p3);
+  }
+}
+
+template <typename LT>
+__device__ void solve_blocked(const LT* M, const LT* invd, int S, int ld, LT* v) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int kb = 0; kb < S; kb += NB) {
+    const int nb = min(NB, S - kb), ke = kb + nb;
+    if (warp == 0) {
+      LT acc = LT(0);
+      const LT* row = M + (kb + min(lane, nb - 1)) * ld + kb;
+      if (lane < nb) {
+        acc = v[kb + lane];
+#pragma unroll
+        for (int c = 0; c < NB - 1; ++c)
+          if (c < lane) acc += row[c] * v[kb + c];
+      }
+      __syncwarp();
+      if (lane < nb) v[kb + lane] = acc;
+    }
+    __syncthreads();
+    if (nb == NB)
+      rows_minus_block<LT, true>(M + kb, ld, v + kb, nb, v, ke, S);
+    else
+      rows_minus_block<LT, false>(M + kb, ld, v + kb, nb, v, ke, S);
+    __syncthreads();
+  }
+  for (int kb = ((S - 1) / NB) * NB; kb >= 0; kb -= NB) {
+    const int nb = min(NB, S - kb);
+    if (warp == 0) {
+      LT acc = LT(0);
+      const LT* row = M + (kb + min(lane, nb - 1)) * ld + kb;
+      if (lane < nb) {
+        acc = invd[kb + lane] * v[kb + lane];
+#pragma unroll
+        for (int c = 1; c < NB; ++c)
+          if (c > lane && c < nb) acc += row[c] * v[kb + c];
+      }
+      __syncwarp();
+      if (lane < nb) v[kb + lane] = acc;
+    }
+    __syncthreads();
+    if (nb == NB)
+      rows_minus_block<LT, true>(M + kb, ld, v + kb, nb, v, 0, kb);
+    else
+      rows_minus_block<LT, false>(M + kb, ld, v + kb, nb, v, 0, kb);
     __syncthreads();
   }
 }
@@ -296,7 +673,7 @@ __host__ __device__ inline size_t layout(int S, int R, int nseg, bool mixed, uns
     return p;
   };
   Smem t;
-  t.M = take((size_t)S * S * lt);
+  t.M = take((size_t)S * lead_dim(S) * lt);
   t.invd = take((size_t)S * lt);
   t.D = (double*)take((size_t)kDiffRows * S * 8);
   t.y = (double*)take(S * 8);
@@ -384,8 +761,8 @@ __device__ void linear_solve<double>(Cell<double>& c, double cc, const double* w
   const int S = c.n.S;
   for (int i = threadIdx.x; i < S; i += NT) dy[i] = w[i];
   __syncthreads();
-  forward_solve<double>((const double*)c.s.M, S, dy);
-  backward_solve<double>((const double*)c.s.M, (const double*)c.s.invd, S, dy);
+  forward_crout64((const double*)c.s.M, (const double*)c.s.invd, S, dy);
+  backward_crout64((const double*)c.s.M, S, dy);
 }
 
 // FP32 LU solve, then FP64 residual w - (dy - c J dy) against the FP64
@@ -397,10 +774,10 @@ __device__ void linear_solve<float>(Cell<float>& c, double cc, const double* w, 
   const float* M = (const float*)c.s.M;
   const float* invd = (const float*)c.s.invd;
   float* v = c.s.v32;
+  const int ld = lead_dim(S);
   for (int i = threadIdx.x; i < S; i += NT) v[i] = (float)w[i];
   __syncthreads();
-  forward_solve<float>(M, S, v);
-  backward_solve<float>(M, invd, S, v);
+  solve_blocked<float>(M, invd, S, ld, v);
   for (int i = threadIdx.x; i < S; i += NT) dy[i] = (double)v[i];
   __syncthreads();
   for (int sweep = 0; sweep < c.a.max_refine; ++sweep) {
@@ -412,8 +789,7 @@ __device__ void linear_solve<float>(Cell<float>& c, double cc, const double* w, 
       v[i] = (float)res;
     }
     __syncthreads();
-    forward_solve<float>(M, S, v);
-    backward_solve<float>(M, invd, S, v);
+    solve_blocked<float>(M, invd, S, ld, v);
     double sq = 0.0;
     for (int i = threadIdx.x; i < S; i += NT) {
       const double corr = (double)v[i];
@@ -430,7 +806,10 @@ __device__ void linear_solve<float>(Cell<float>& c, double cc, const double* w, 
 template <typename LT>
 __device__ void factor(Cell<LT>& c, double cc) {
   build_matrix<LT>(c.n, c.Jv, cc, (LT*)c.s.M);
-  lu_factor<LT>(c.n, (LT*)c.s.M, (LT*)c.s.invd);
+  if constexpr (sizeof(LT) == 4)
+    lu_blocked<LT>((LT*)c.s.M, (LT*)c.s.invd, c.n.S, lead_dim(c.n.S));
+  else
+    lu_crout64(c.n, (double*)c.s.M, (double*)c.s.invd);
   c.st.lu_factors++;
 }
 
@@ -482,6 +861,7 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
   const DevNet& n = a.net;
   const int S = n.S;
   Cell<LT> c{a, n, s, ws, ws + n.R, ws + 3 * n.R, {}};
+  c.st.t_begin_ns = (long long)globaltimer();
   const cbx_cell_params p = a.phi[cell];
   int status = CBX_CELL_OK;
   for (int i = threadIdx.x; i < S; i += NT) s.y[i] = a.x0[(size_t)__ldg(n.perm + i) * a.C + cell];
@@ -627,6 +1007,7 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
   }
   if (threadIdx.x == 0) {
     a.status[cell] = status;
+    c.st.t_end_ns = (long long)globaltimer();
     if (a.stats) a.stats[cell] = c.st;
   }
   __syncthreads();

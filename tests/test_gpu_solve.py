@@ -32,7 +32,7 @@ def dev():
 def gpu_solve(N, phi, x0, t_end, dev, **kw):
     phi_d = torch.tensor(np.asarray(phi), dtype=torch.float64, device=dev).contiguous()
     x0_d = torch.tensor(np.asarray(x0), dtype=torch.float64, device=dev).contiguous()
-    stats = torch.zeros((phi_d.shape[0], 10), dtype=torch.int32, device=dev)
+    stats = carbox.stats_tensor(phi_d.shape[0], dev)
     x, st, stats = carbox.solve(N, phi_d, x0_d, 0.0, t_end, carbox.options(**kw), stats=stats)
     torch.cuda.synchronize()
     return x.cpu().numpy(), st.cpu().numpy(), stats.cpu().numpy()
@@ -62,7 +62,7 @@ def test_single_cell_32(dev, net32, prec):
     assert st[0] == carbox.CBX_CELL_OK
     assert_twin(x[:, 0], ref.x, "32-species cell")
     assert_conserved(net32, x0, x[:, 0])
-    s = dict(zip(carbox.STATS_FIELDS, stats[0]))
+    s = {k: int(v[0]) for k, v in carbox.stats_dict(stats).items()}
     print("gpu", s, "\noracle", ref.stats)
     assert abs(s["steps"] - ref.stats["steps"]) <= 0.02 * ref.stats["steps"]
 
