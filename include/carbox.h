@@ -189,6 +189,37 @@ int cbx_solve_host(cbx_network* net, const cbx_cell_params* phi, const double* x
                    double t_end, const cbx_options* opt, void* stream, double* x_out,
                    int* cell_status, cbx_cell_stats* stats);
 
+/*
+ * cbx_solve for callers that cannot allocate GPU memory while they run. The
+ * paper has no counterpart: this is a deployment variant of cbx_solve with the
+ * same arguments, the same kernel and bitwise the same results.
+ *
+ * cbx_solve takes its scratch (per-CTA rate/Jacobian workspace and a next-cell
+ * counter) from the stream-ordered allocator on every call. Hosts that reserve
+ * all device memory up front and forbid later allocation by library code,
+ * latency-critical loops that must not enter the driver's allocator, and
+ * processes running at their memory budget cannot allow that. This entry
+ * point calls no cudaMalloc, cudaFree or other allocating routine: its scratch
+ * is a fixed 16 MiB array compiled into the library, which every GPU that
+ * loads the library holds until the process exits.
+ *
+ * - Set-up: the first call made with a given device current looks up the
+ *   array's device address (cudaGetSymbolAddress) and caches it; make that
+ *   first call before any stream capture.
+ * - The network's tables must already be on the current device (they are
+ *   uploaded by cbx_network_create when a GPU is present); otherwise CBX_E_ARG.
+ * - Limit: a network whose per-CTA scratch (8 * (3 R + nnz(J)) bytes, rounded
+ *   up) exceeds the array is rejected with CBX_E_TOO_LARGE. When fewer CTAs
+ *   fit than the device can run, fewer are launched (slower, same results).
+ * - All calls share the one array and it keeps the last call's contents; the
+ *   counter is cleared on `stream` at every call (cudaMemsetAsync). Calls
+ *   whose kernels overlap on the GPU (other streams, other host threads) race
+ *   on the array: issue them on one stream, one after another.
+ */
+int cbx_solve_noalloc(cbx_network* net, const cbx_cell_params* phi, const double* x0, int C, double t0,
+                      double t_end, const cbx_options* opt, void* stream, double* x_out, int* cell_status,
+                      cbx_cell_stats* stats);
+
 #ifdef __cplusplus
 }
 #endif

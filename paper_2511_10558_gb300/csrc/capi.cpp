@@ -13,13 +13,6 @@
 
 using namespace cbx;
 
-struct cbx_network {
-  HostNet host;
-  DevNet dev;
-  void* dbuf = nullptr;  // one device allocation holding every table
-  int device = 0;
-  std::mutex mu;
-};
 
 namespace {
 
@@ -110,6 +103,11 @@ int upload(cbx_network* n) {
 }
 
 }  // namespace
+
+namespace cbx {
+// Record an error message for cbx_last_error() from another translation unit.
+int record_error(int code, const std::string& msg) { return fail(code, msg); }
+}  // namespace cbx
 
 extern "C" {
 

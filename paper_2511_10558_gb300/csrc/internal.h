@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -84,6 +85,17 @@ int launch_solver(const SolveArgs& a, bool mixed, int grid, void* stream);
 // CTAs per SM the solver can keep resident (0 if it cannot launch).
 int solver_occupancy(int S, int R, int nseg, bool mixed);
 int device_sm_count();
+// Set the calling thread's cbx_last_error() message; returns code.
+int record_error(int code, const std::string& msg);
 size_t device_smem_optin();
 
 }  // namespace cbx
+
+// Library-side network object behind the opaque cbx_network handle.
+struct cbx_network {
+  cbx::HostNet host;
+  cbx::DevNet dev;
+  void* dbuf = nullptr;  // one device allocation holding every table
+  int device = 0;
+  std::mutex mu;
+};
