@@ -8,6 +8,10 @@ e- = C+, others 1e-20; integrated 0 -> 1 Myr at rtol 1e-4, atol 1e-20 in
 plain FP64. One step = one solve of the whole batch.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--cells C] [--only fp64|mixed] [--no-e2e] [--no-cpu-baseline]
+
+(--cells / --only / --no-e2e shrink the run for profiler captures; the default
+run is the benchmark.)
 
 With N > 1 (torchrun) each rank solves its own 16,384 cells of a batch of
 N x 16,384 (weak scaling, no collective on the data path); the barrier and the
@@ -33,7 +37,8 @@ sys.path.insert(0, ROOT)
 from paper_2511_10558_gb300 import synth  # noqa: E402
 
 METRIC = "cell-solves/s to 1 Myr at rtol 1e-4 (150/500 sp), FP64 vs mixed; p50/p99 latency"
-S_SP, R_RX, CELLS = 150, 1500, 16384
+S_SP, R_RX = 150, 1500
+CELLS = 16384  # per GPU (overridden by --cells for profiler captures)
 T_END = 1e6 * synth.YEAR
 RTOL, ATOL = 1e-4, 1e-20
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (152 SMs x 2 FMA/clk x 2.07 GHz); 1.19 measured by FMA chains
@@ -190,6 +195,8 @@ def run_reference(args):
 # ------------------------------------------------------------------ GPU arm
 
 def run_gpu(args):
+    global CELLS
+    CELLS = args.cells
     import torch
     ws, rank, local = _dist()
     if ws > 1:
@@ -246,7 +253,7 @@ def run_gpu(args):
 
     # ---- FP64 (headline)
     with ClockSampler(local) as clk:
-        ms64 = timed(carbox.CBX_FP64, args.steps, args.warmup)
+        ms64 = timed(carbox.CBX_FP64, args.steps, args.warmup) if args.only != "mixed" else [float("nan")]
     st64 = carbox.stats_dict(stats.cpu().numpy())
     ok64 = int((status == 0).sum().item())
     t_local = sum(ms64) / 1e3
@@ -263,7 +270,14 @@ def run_gpu(args):
     achieved = fp64_flops / (ms_per_step / 1e3) / 1e12
 
     # ---- mixed precision, same workload
-    msmx = timed(carbox.CBX_MIXED, max(1, args.steps), 1)
+    if args.only == "fp64":
+        print(json.dumps({"only": "fp64", "cells": CELLS, "ms_per_step": ms_per_step, "value": value}), flush=True)
+        return
+    msmx = timed(carbox.CBX_MIXED, max(1, args.steps), 1 if args.only != "mixed" else args.warmup)
+    if args.only == "mixed":
+        print(json.dumps({"only": "mixed", "cells": CELLS, "ms_per_step": sum(msmx) / len(msmx),
+                          "value": CELLS * len(msmx) / (sum(msmx) / 1e3)}), flush=True)
+        return
     stmx = carbox.stats_dict(stats.cpu().numpy())
     okmx = int((status == 0).sum().item())
     mixed_value = CELLS * len(msmx) / (sum(msmx) / 1e3)
@@ -271,14 +285,14 @@ def run_gpu(args):
 
     # ---- end to end through the host-buffer C-ABI call (copies inside the timed region)
     opt = carbox.options(rtol=RTOL, atol=ATOL, precision=carbox.CBX_FP64)
-    e2e_steps = max(1, min(args.steps, 2))
+    e2e_steps = max(1, min(args.steps, 2)) if not args.no_e2e else 0
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         xh, sh, _ = carbox.solve_host(N, phi_h, x0_h.reshape(S_SP, CELLS), 0.0, T_END, opt, stream=stream)
     barrier()
-    e2e_t = time.perf_counter() - t0
-    e2e_value = ws * CELLS * e2e_steps / e2e_t if ws == 1 else None
+    e2e_t = max(time.perf_counter() - t0, 1e-9)
+    e2e_value = ws * CELLS * e2e_steps / e2e_t if ws == 1 and e2e_steps else None
     if ws > 1:
         tt = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
@@ -338,6 +352,9 @@ def main():
     ap.add_argument("--impl", default="carbox", choices=["carbox", "reference"])
     ap.add_argument("--ref-cells", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cells", type=int, default=16384)
+    ap.add_argument("--only", choices=["fp64", "mixed"], default=None)
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
