@@ -168,8 +168,8 @@ int cbx_network_info(const cbx_network* net, cbx_netinfo* out) {
   out->nnz_lu = h.nnzLU;
   out->lu_flops = h.lu_flops;
   out->lu_flops_dense = 2.0 * h.S * (double)h.S * h.S / 3.0;
-  out->smem_bytes_fp64 = (int)smem_bytes(h.S, h.R, h.nseg, false);
-  out->smem_bytes_mixed = (int)smem_bytes(h.S, h.R, h.nseg, true);
+  out->smem_bytes_fp64 = (int)smem_bytes(h.S, h.R, h.nseg, false, false);
+  out->smem_bytes_mixed = (int)smem_bytes(h.S, h.R, h.nseg, true, false);
   return CBX_OK;
 }
 
@@ -190,11 +190,12 @@ int cbx_solve(cbx_network* net, const cbx_cell_params* phi, const double* x0, in
   if (rc) return rc;
   const HostNet& h = net->host;
   const bool mixed = o.precision == CBX_MIXED;
-  const int occ = solver_occupancy(h.S, h.R, h.nseg, mixed);
+  const SolverPlan plan = plan_solver(h.S, h.R, h.nseg, h.nnzJ, mixed);
+  const int occ = plan.occupancy;
   if (occ < 1) {
-    char m[160];
-    snprintf(m, sizeof m, "network (S=%d, R=%d) needs %zu B of shared memory per CTA; the device allows %zu",
-             h.S, h.R, smem_bytes(h.S, h.R, h.nseg, mixed), device_smem_optin());
+    char m[200];
+    snprintf(m, sizeof m, "network (S=%d, R=%d) needs %zu B of shared memory per CTA (S <= %d); the device allows %zu",
+             h.S, h.R, plan.smem, 512, device_smem_optin());
     return fail(CBX_E_TOO_LARGE, m);
   }
   const int grid = std::min(C, occ * device_sm_count());
@@ -220,7 +221,7 @@ int cbx_solve(cbx_network* net, const cbx_cell_params* phi, const double* x0, in
   a.x_out = x_out;
   a.status = cell_status;
   a.stats = stats;
-  a.ws_stride = workspace_doubles(h.S, h.R, h.nnzJ);
+  a.ws_stride = plan.ws_stride;
   const size_t ws_bytes = (size_t)grid * a.ws_stride * sizeof(double) + 256;
   void* ws = nullptr;
   cudaError_t e = cudaMallocAsync(&ws, ws_bytes, st);
@@ -228,7 +229,7 @@ int cbx_solve(cbx_network* net, const cbx_cell_params* phi, const double* x0, in
   a.ws = (double*)ws;
   a.counter = (int*)((char*)ws + (size_t)grid * a.ws_stride * sizeof(double));
   e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
-  if (e == cudaSuccess) e = (cudaError_t)launch_solver(a, mixed, grid, stream);
+  if (e == cudaSuccess) e = (cudaError_t)launch_solver(a, plan, grid, stream);
   cudaError_t e2 = cudaFreeAsync(ws, st);
   if (e != cudaSuccess) return cuda_fail(e, "solver launch");
   if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync(workspace)");

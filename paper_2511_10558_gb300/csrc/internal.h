@@ -76,14 +76,19 @@ struct SolveArgs {
   int* counter;    // next-cell counter, zero before the launch
 };
 
-// Shared-memory bytes per CTA of the smem solver (mixed = FP32 matrix).
-size_t smem_bytes(int S, int R, int nseg, bool mixed);
-// Per-CTA global workspace, in doubles.
-long long workspace_doubles(int S, int R, int nnzJ);
-// Launch the smem solver; returns a cudaError_t value.
-int launch_solver(const SolveArgs& a, bool mixed, int grid, void* stream);
-// CTAs per SM the solver can keep resident (0 if it cannot launch).
-int solver_occupancy(int S, int R, int nseg, bool mixed);
+// Launch plan of the solver kernel for one network and precision: matrix in
+// shared memory (gm = false) or in the CTA's global workspace (gm = true).
+struct SolverPlan {
+  bool mixed = false, gm = false;
+  size_t smem = 0;          // dynamic shared memory per CTA
+  long long ws_stride = 0;  // per-CTA global workspace, in doubles
+  int occupancy = 0;        // CTAs per SM (0: cannot launch)
+};
+size_t smem_bytes(int S, int R, int nseg, bool mixed, bool gm);
+long long workspace_doubles(int S, int R, int nnzJ, bool mixed, bool gm);
+SolverPlan plan_solver(int S, int R, int nseg, int nnzJ, bool mixed);
+// Launch the solver; returns a cudaError_t value.
+int launch_solver(const SolveArgs& a, const SolverPlan& p, int grid, void* stream);
 int device_sm_count();
 // Set the calling thread's cbx_last_error() message; returns code.
 int record_error(int code, const std::string& msg);

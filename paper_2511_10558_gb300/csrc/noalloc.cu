@@ -76,9 +76,10 @@ extern "C" int cbx_solve_noalloc(cbx_network* net, const cbx_cell_params* phi, c
   }
   const HostNet& h = net->host;
   const bool mixed = o.precision == CBX_MIXED;
-  const int occ = solver_occupancy(h.S, h.R, h.nseg, mixed);
-  if (occ < 1) return fail(CBX_E_TOO_LARGE, "network too large for the shared-memory solver");
-  const long long stride = workspace_doubles(h.S, h.R, h.nnzJ);
+  const SolverPlan plan = plan_solver(h.S, h.R, h.nseg, h.nnzJ, mixed);
+  const int occ = plan.occupancy;
+  if (occ < 1) return fail(CBX_E_TOO_LARGE, "network too large for the solver");
+  const long long stride = plan.ws_stride;
   const long long fit = (long long)((kScratchBytes - kCounterBytes) / (stride * sizeof(double)));
   if (fit < 1) {
     char m[200];
@@ -113,7 +114,7 @@ extern "C" int cbx_solve_noalloc(cbx_network* net, const cbx_cell_params* phi, c
   a.ws = (double*)((unsigned char*)scratch + kCounterBytes);
   e = cudaMemsetAsync(a.counter, 0, sizeof(int), (cudaStream_t)stream);
   if (e != cudaSuccess) return fail(CBX_E_CUDA, std::string("cudaMemsetAsync(counter): ") + cudaGetErrorString(e));
-  e = (cudaError_t)launch_solver(a, mixed, grid, stream);
+  e = (cudaError_t)launch_solver(a, plan, grid, stream);
   if (e != cudaSuccess) return fail(CBX_E_CUDA, std::string("solver launch: ") + cudaGetErrorString(e));
   return CBX_OK;
 }

@@ -411,71 +411,96 @@ constexpr int NB = 32;  // panel width
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
-template <typename LT, bool FULL>
+template <typename LT, bool FULL, int RPT>
 __device__ __forceinline__ void panel_factor(LT* M, LT* invd, int S, int ld, int kb, int nb) {
   const int tid = threadIdx.x;
-  const int i = kb + tid;
-  const bool own = i < S;
-  LT r[NB];
+  LT r[RPT][NB];
 #pragma unroll
-  for (int jj = 0; jj < NB; ++jj) r[jj] = own && (FULL || jj < nb) ? M[i * ld + kb + jj] : LT(0);
+  for (int p = 0; p < RPT; ++p) {
+    const int i = kb + tid + NT * p;
+#pragma unroll
+    for (int jj = 0; jj < NB; ++jj) r[p][jj] = i < S && (FULL || jj < nb) ? M[i * ld + kb + jj] : LT(0);
+  }
 #pragma unroll
   for (int c = 0; c < NB; ++c) {
     if (FULL || c < nb) {
       const int k = kb + c;
-      if (i == k) {
+      if (tid == k - kb) {  // the pivot row is row kb + c, owned by thread c (p = 0)
 #pragma unroll
         for (int jj = c; jj < NB; ++jj)
-          if (FULL || jj < nb) M[k * ld + kb + jj] = r[jj];
+          if (FULL || jj < nb) M[k * ld + kb + jj] = r[0][jj];
       }
       __syncthreads();
       const LT* prow = M + k * ld + kb;
-      if (own && i > k) {
-        const LT l = r[c] * recip(prow[c]);
-        r[c] = l;
+      const LT inv = recip(prow[c]);
 #pragma unroll
-        for (int jj = c + 1; jj < NB; ++jj)
-          if (FULL || jj < nb) r[jj] -= l * prow[jj];
+      for (int p = 0; p < RPT; ++p) {
+        const int i = kb + tid + NT * p;
+        if (i < S && i > k) {
+          const LT l = r[p][c] * inv;
+          r[p][c] = l;
+#pragma unroll
+          for (int jj = c + 1; jj < NB; ++jj)
+            if (FULL || jj < nb) r[p][jj] -= l * prow[jj];
+        }
       }
-      if (tid == 0) invd[k] = recip(prow[c]);
+      if (tid == 0) invd[k] = inv;
     }
   }
   __syncthreads();
-  if (own && i >= kb + nb) {
 #pragma unroll
-    for (int jj = 0; jj < NB; ++jj)
-      if (FULL || jj < nb) M[i * ld + kb + jj] = r[jj];
-  } else if (own) {
+  for (int p = 0; p < RPT; ++p) {
+    const int i = kb + tid + NT * p;
+    if (i >= S) continue;
+    if (i >= kb + nb) {
 #pragma unroll
-    for (int jj = 0; jj < NB; ++jj)
-      if (kb + jj < i) M[i * ld + kb + jj] = r[jj];
+      for (int jj = 0; jj < NB; ++jj)
+        if (FULL || jj < nb) M[i * ld + kb + jj] = r[p][jj];
+    } else {
+      // rows of the diagonal block: only their L part (columns < own row) is new
+#pragma unroll
+      for (int jj = 0; jj < NB; ++jj)
+        if (kb + jj < i) M[i * ld + kb + jj] = r[p][jj];
+    }
   }
   __syncthreads();
 }
 
+// Forward substitution of one column (NB values in registers) with the unit
+// lower L11 of the panel.
+template <typename LT, bool FULL>
+__device__ __forceinline__ void l11_solve(const LT* L, int ld, int nb, LT (&v)[NB]) {
+#pragma unroll
+  for (int c = 0; c < NB - 1; ++c) {
+#pragma unroll
+    for (int r = c + 1; r < NB; ++r)
+      if (FULL || r < nb) v[r] -= L[r * ld + c] * v[c];
+  }
+}
+
 template <typename LT, bool FULL>
 __device__ __forceinline__ void panel_u12(LT* M, int S, int ld, int kb, int nb) {
-  const int ke = kb + nb, ncol = S - ke, t = threadIdx.x;
-  const bool a12 = t < ncol, ident = !a12 && t < ncol + nb;
-  const int col = ke + t, jj = t - ncol;
-  LT v[NB];
+  const int ke = kb + nb, ncol = S - ke;
+  const LT* L = M + kb * ld + kb;
+  // U12 = L11^{-1} A12, one column per thread (A12 does not overlap L11)
+  for (int t = threadIdx.x; t < ncol; t += NT) {
+    const int col = ke + t;
+    LT v[NB];
 #pragma unroll
-  for (int r = 0; r < NB; ++r) v[r] = a12 && (FULL || r < nb) ? M[(kb + r) * ld + col] : (ident && r == jj ? LT(1) : LT(0));
-  if (a12 || ident) {
-    const LT* L = M + kb * ld + kb;
-#pragma unroll
-    for (int c = 0; c < NB - 1; ++c) {
-#pragma unroll
-      for (int r = c + 1; r < NB; ++r)
-        if (FULL || r < nb) v[r] -= L[r * ld + c] * v[c];
-    }
-  }
-  __syncthreads();
-  if (a12) {
+    for (int r = 0; r < NB; ++r) v[r] = FULL || r < nb ? M[(kb + r) * ld + col] : LT(0);
+    l11_solve<LT, FULL>(L, ld, nb, v);
 #pragma unroll
     for (int r = 0; r < NB; ++r)
       if (FULL || r < nb) M[(kb + r) * ld + col] = v[r];
-  } else if (ident) {
+  }
+  // L11^{-1}: identity columns, written over L11 after everyone has read it
+  const int jj = threadIdx.x;
+  LT v[NB];
+#pragma unroll
+  for (int r = 0; r < NB; ++r) v[r] = r == jj ? LT(1) : LT(0);
+  if (jj < nb) l11_solve<LT, FULL>(L, ld, nb, v);
+  __syncthreads();
+  if (jj < nb) {
 #pragma unroll
     for (int r = 0; r < NB; ++r)
       if (r > jj && (FULL || r < nb)) M[(kb + r) * ld + kb + jj] = v[r];
@@ -483,40 +508,40 @@ __device__ __forceinline__ void panel_u12(LT* M, int S, int ld, int kb, int nb) 
   __syncthreads();
 }
 
-// A22 -= L21 U12 over rows/cols [ke, S): warps take 4-row strips, lanes the
+// A22 -= L21 U12 over rows/cols [ke, S): warps take TR-row strips, lanes the
 // columns ke + lane + 32 g (exactly NG groups); the inner dimension is nb.
-template <typename LT, int NG>
+template <typename LT, int NG, int TR>
 __device__ __forceinline__ void trailing_update_ng(LT* M, int S, int ld, int kb, int nb) {
   const int ke = kb + nb, ncol = S - ke;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   bool colok[NG];
 #pragma unroll
   for (int g = 0; g < NG; ++g) colok[g] = lane + 32 * g < ncol;
-  for (int rs = warp; rs * 4 < ncol; rs += NW) {
-    const int i0 = ke + rs * 4;
-    LT acc[4][NG];
+  for (int rs = warp; rs * TR < ncol; rs += NW) {
+    const int i0 = ke + rs * TR;
+    LT acc[TR][NG];
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < TR; ++r)
 #pragma unroll
       for (int g = 0; g < NG; ++g) acc[r][g] = LT(0);
-    const LT* lp[4];
+    const LT* lp[TR];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) lp[r] = M + min(i0 + r, S - 1) * ld + kb;
+    for (int r = 0; r < TR; ++r) lp[r] = M + min(i0 + r, S - 1) * ld + kb;
     const LT* up = M + kb * ld + ke + lane;
     for (int c = 0; c < nb; ++c) {
-      LT lv[4], uu[NG];
+      LT lv[TR], uu[NG];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) lv[r] = lp[r][c];
+      for (int r = 0; r < TR; ++r) lv[r] = lp[r][c];
 #pragma unroll
       for (int g = 0; g < NG; ++g) uu[g] = colok[g] ? up[32 * g] : LT(0);
 #pragma unroll
       for (int g = 0; g < NG; ++g)
 #pragma unroll
-        for (int r = 0; r < 4; ++r) acc[r][g] += lv[r] * uu[g];
+        for (int r = 0; r < TR; ++r) acc[r][g] += lv[r] * uu[g];
       up += ld;
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < TR; ++r) {
       if (i0 + r < S) {
         LT* row = M + (i0 + r) * ld + ke + lane;
 #pragma unroll
@@ -527,41 +552,67 @@ __device__ __forceinline__ void trailing_update_ng(LT* M, int S, int ld, int kb,
   }
 }
 
-template <typename LT>
+template <typename LT, bool LARGE>
 __device__ __forceinline__ void trailing_update(LT* M, int S, int ld, int kb, int nb) {
   const int ncol = S - kb - nb;
   if (ncol <= 0) return;
+  if (!LARGE) {
+    switch ((ncol + 31) >> 5) {
+      case 1: trailing_update_ng<LT, 1, 4>(M, S, ld, kb, nb); break;
+      case 2: trailing_update_ng<LT, 2, 4>(M, S, ld, kb, nb); break;
+      case 3: trailing_update_ng<LT, 3, 4>(M, S, ld, kb, nb); break;
+      case 4: trailing_update_ng<LT, 4, 4>(M, S, ld, kb, nb); break;
+      case 5: trailing_update_ng<LT, 5, 4>(M, S, ld, kb, nb); break;
+      case 6: trailing_update_ng<LT, 6, 4>(M, S, ld, kb, nb); break;
+      case 7: trailing_update_ng<LT, 7, 4>(M, S, ld, kb, nb); break;
+      default: trailing_update_ng<LT, 8, 4>(M, S, ld, kb, nb); break;
+    }
+    __syncthreads();
+    return;
+  }
   switch ((ncol + 31) >> 5) {
-    case 1: trailing_update_ng<LT, 1>(M, S, ld, kb, nb); break;
-    case 2: trailing_update_ng<LT, 2>(M, S, ld, kb, nb); break;
-    case 3: trailing_update_ng<LT, 3>(M, S, ld, kb, nb); break;
-    case 4: trailing_update_ng<LT, 4>(M, S, ld, kb, nb); break;
-    case 5: trailing_update_ng<LT, 5>(M, S, ld, kb, nb); break;
-    case 6: trailing_update_ng<LT, 6>(M, S, ld, kb, nb); break;
-    case 7: trailing_update_ng<LT, 7>(M, S, ld, kb, nb); break;
-    default: trailing_update_ng<LT, 8>(M, S, ld, kb, nb); break;
+    case 1: trailing_update_ng<LT, 1, 4>(M, S, ld, kb, nb); break;
+    case 2: trailing_update_ng<LT, 2, 4>(M, S, ld, kb, nb); break;
+    case 3: trailing_update_ng<LT, 3, 4>(M, S, ld, kb, nb); break;
+    case 4: trailing_update_ng<LT, 4, 4>(M, S, ld, kb, nb); break;
+    case 5: trailing_update_ng<LT, 5, 4>(M, S, ld, kb, nb); break;
+    case 6: trailing_update_ng<LT, 6, 4>(M, S, ld, kb, nb); break;
+    case 7: trailing_update_ng<LT, 7, 4>(M, S, ld, kb, nb); break;
+    case 8: trailing_update_ng<LT, 8, 4>(M, S, ld, kb, nb); break;
+    case 9: trailing_update_ng<LT, 9, 2>(M, S, ld, kb, nb); break;
+    case 10: trailing_update_ng<LT, 10, 2>(M, S, ld, kb, nb); break;
+    case 11: trailing_update_ng<LT, 11, 2>(M, S, ld, kb, nb); break;
+    case 12: trailing_update_ng<LT, 12, 2>(M, S, ld, kb, nb); break;
+    case 13: trailing_update_ng<LT, 13, 2>(M, S, ld, kb, nb); break;
+    case 14: trailing_update_ng<LT, 14, 2>(M, S, ld, kb, nb); break;
+    case 15: trailing_update_ng<LT, 15, 2>(M, S, ld, kb, nb); break;
+    default: trailing_update_ng<LT, 16, 2>(M, S, ld, kb, nb); break;
   }
   __syncthreads();
 }
 
-template <typename LT>
+// LARGE: networks of 257..512 species (matrix in global memory): two panel
+// rows per thread and up to 16 column groups in the trailing update.
+template <typename LT, bool LARGE>
 __device__ void lu_blocked(LT* M, LT* invd, int S, int ld) {
   for (int kb = 0; kb < S; kb += NB) {
     const int nb = min(NB, S - kb);
+    const bool two = LARGE && S - kb > NT;  // more panel rows than threads
     if (nb == NB) {
-      panel_factor<LT, true>(M, invd, S, ld, kb, nb);
+      if (two) panel_factor<LT, true, LARGE ? 2 : 1>(M, invd, S, ld, kb, nb);
+      else panel_factor<LT, true, 1>(M, invd, S, ld, kb, nb);
       panel_u12<LT, true>(M, S, ld, kb, nb);
     } else {
-      panel_factor<LT, false>(M, invd, S, ld, kb, nb);
+      panel_factor<LT, false, 1>(M, invd, S, ld, kb, nb);
       panel_u12<LT, false>(M, S, ld, kb, nb);
     }
-    trailing_update<LT>(M, S, ld, kb, nb);
+    trailing_update<LT, LARGE>(M, S, ld, kb, nb);
   }
-  // U_bb^{-1}: thread per column of each diagonal block, all blocks at once
-  {
-    const int tid = threadIdx.x;
-    const int nblk = (S + NB - 1) / NB;
-    const int b = tid / NB, jj = tid % NB;
+  // U_bb^{-1}: thread per column of each diagonal block, NT / NB blocks at a
+  // time; a chunk's reads finish before its writes
+  const int nblk = (S + NB - 1) / NB;
+  for (int b0 = 0; b0 < nblk; b0 += NT / NB) {
+    const int b = b0 + threadIdx.x / NB, jj = threadIdx.x % NB;
     LT x[NB];
     const bool act = b < nblk && b * NB + jj < S;
     const int kb = b * NB;
@@ -586,9 +637,6 @@ __device__ void lu_blocked(LT* M, LT* invd, int S, int ld) {
   }
 }
 
-// v <- (L U)^{-1} v with the blocked factors: per diagonal block one
-// lower-triangular mat-vec by L_bb^{-1}, then a rectangular update of the rows
-// below; backwards the same with U_bb^{-1} (diagonal via invd) and the rows above.
 template <typename LT, bool FULL>
 __device__ __forceinline__ void rows_minus_block(const LT* M, int ld, const LT* vb, int nb, LT* v, int i0, int i1) {
   // v[i] -= sum_c M[i][c] vb[c] for rows i in [i0, i1); M points at column kb
@@ -664,7 +712,7 @@ struct Smem {
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
-__host__ __device__ inline size_t layout(int S, int R, int nseg, bool mixed, unsigned char* base, Smem* s) {
+__host__ __device__ inline size_t layout(int S, int R, int nseg, bool mixed, bool gm, unsigned char* base, Smem* s) {
   const size_t lt = mixed ? sizeof(float) : sizeof(double);
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -673,7 +721,7 @@ __host__ __device__ inline size_t layout(int S, int R, int nseg, bool mixed, uns
     return p;
   };
   Smem t;
-  t.M = take((size_t)S * lead_dim(S) * lt);
+  t.M = take(gm ? 0 : (size_t)S * lead_dim(S) * lt);
   t.invd = take((size_t)S * lt);
   t.D = (double*)take((size_t)kDiffRows * S * 8);
   t.y = (double*)take(S * 8);
@@ -694,12 +742,15 @@ __host__ __device__ inline size_t layout(int S, int R, int nseg, bool mixed, uns
   return off;
 }
 
-size_t smem_bytes(int S, int R, int nseg, bool mixed) { return layout(S, R, nseg, mixed, nullptr, nullptr); }
+size_t smem_bytes(int S, int R, int nseg, bool mixed, bool gm) {
+  return layout(S, R, nseg, mixed, gm, nullptr, nullptr);
+}
 
-long long workspace_doubles(int S, int R, int nnzJ) {
-  (void)S;
-  const long long n = 3LL * R + nnzJ;
-  return (n + 31) / 32 * 32;
+long long workspace_doubles(int S, int R, int nnzJ, bool mixed, bool gm) {
+  long long n = 3LL * R + nnzJ;
+  n = (n + 31) / 32 * 32;
+  if (gm) n += ((long long)S * lead_dim(S) * (mixed ? 4 : 8) / 8 + 31) / 32 * 32;
+  return n;
 }
 
 // ---------------------------------------------------------------- BDF pieces
@@ -741,11 +792,13 @@ __device__ void rescale(double* D, int S, int q, double rho, double* Tm) {
   __syncthreads();
 }
 
-template <typename LT>
+template <typename LT, bool GM>
 struct Cell {
+  static constexpr bool gm = GM;  // M in global memory (blocked LU and solves for both precisions)
   const SolveArgs& a;
   const DevNet& n;
   Smem& s;
+  LT* M;     // Newton matrix: shared memory, or the CTA's global workspace
   double* kap;
   double* g;
   double* Jv;
@@ -753,25 +806,26 @@ struct Cell {
 };
 
 // Solve (I - cJ) dy = w with the factored matrix in shared memory.
-template <typename LT>
-__device__ void linear_solve(Cell<LT>& c, double cc, const double* w, double* dy);
-
-template <>
-__device__ void linear_solve<double>(Cell<double>& c, double cc, const double* w, double* dy) {
+template <bool GM>
+__device__ void linear_solve(Cell<double, GM>& c, double cc, const double* w, double* dy) {
   const int S = c.n.S;
   for (int i = threadIdx.x; i < S; i += NT) dy[i] = w[i];
   __syncthreads();
-  forward_crout64((const double*)c.s.M, (const double*)c.s.invd, S, dy);
-  backward_crout64((const double*)c.s.M, S, dy);
+  if constexpr (GM) {
+    solve_blocked<double>(c.M, (const double*)c.s.invd, S, lead_dim(S), dy);
+  } else {
+    forward_crout64(c.M, (const double*)c.s.invd, S, dy);
+    backward_crout64(c.M, S, dy);
+  }
 }
 
 // FP32 LU solve, then FP64 residual w - (dy - c J dy) against the FP64
 // Jacobian and FP32 correction solves until the weighted RMS of the
 // correction is <= refine_tol or max_refine sweeps.
-template <>
-__device__ void linear_solve<float>(Cell<float>& c, double cc, const double* w, double* dy) {
+template <bool GM>
+__device__ void linear_solve(Cell<float, GM>& c, double cc, const double* w, double* dy) {
   const int S = c.n.S;
-  const float* M = (const float*)c.s.M;
+  const float* M = c.M;
   const float* invd = (const float*)c.s.invd;
   float* v = c.s.v32;
   const int ld = lead_dim(S);
@@ -803,19 +857,23 @@ __device__ void linear_solve<float>(Cell<float>& c, double cc, const double* w, 
   }
 }
 
-template <typename LT>
-__device__ void factor(Cell<LT>& c, double cc) {
-  build_matrix<LT>(c.n, c.Jv, cc, (LT*)c.s.M);
-  if constexpr (sizeof(LT) == 4)
-    lu_blocked<LT>((LT*)c.s.M, (LT*)c.s.invd, c.n.S, lead_dim(c.n.S));
-  else
-    lu_crout64(c.n, (double*)c.s.M, (double*)c.s.invd);
+template <typename LT, bool GM>
+__device__ void factor(Cell<LT, GM>& c, double cc) {
+  build_matrix<LT>(c.n, c.Jv, cc, c.M);
+  if constexpr (GM) {
+    lu_blocked<LT, true>(c.M, (LT*)c.s.invd, c.n.S, lead_dim(c.n.S));
+  } else {
+    if constexpr (sizeof(LT) == 4)
+      lu_blocked<LT, false>(c.M, (LT*)c.s.invd, c.n.S, lead_dim(c.n.S));
+    else
+      lu_crout64(c.n, c.M, (double*)c.s.invd);
+  }
   c.st.lu_factors++;
 }
 
 // Simplified Newton on d - c f(yp + d) + psi = 0. Leaves y = yp + d, dv = d.
-template <typename LT>
-__device__ bool newton(Cell<LT>& c, double cc, int* iters) {
+template <typename LT, bool GM>
+__device__ bool newton(Cell<LT, GM>& c, double cc, int* iters) {
   const int S = c.n.S;
   Smem& s = c.s;
   for (int i = threadIdx.x; i < S; i += NT) {
@@ -834,7 +892,7 @@ __device__ bool newton(Cell<LT>& c, double cc, int* iters) {
     if (__syncthreads_or(bad)) break;
     for (int i = threadIdx.x; i < S; i += NT) s.w[i] = cc * s.f[i] - s.psi[i] - s.dv[i];
     __syncthreads();
-    linear_solve<LT>(c, cc, s.w, s.dy);
+    linear_solve(c, cc, s.w, s.dy);
     const double dyn = wrms(s.dy, s.wsc, 1.0, S, s.red);
     if (k > 0) {
       rate = dyn / dy_old;
@@ -856,11 +914,13 @@ __device__ bool newton(Cell<LT>& c, double cc, int* iters) {
   return conv;
 }
 
-template <typename LT>
+template <typename LT, bool GM>
 __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
   const DevNet& n = a.net;
   const int S = n.S;
-  Cell<LT> c{a, n, s, ws, ws + n.R, ws + 3 * n.R, {}};
+  // workspace: kappa [R], partials [2R], J values [nnzJ], then (GM) the matrix
+  LT* M = GM ? (LT*)(ws + (3LL * n.R + n.nnzJ + 31) / 32 * 32) : (LT*)s.M;
+  Cell<LT, GM> c{a, n, s, M, ws, ws + n.R, ws + 3 * n.R, {}};
   c.st.t_begin_ns = (long long)globaltimer();
   const cbx_cell_params p = a.phi[cell];
   int status = CBX_CELL_OK;
@@ -941,10 +1001,10 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
         int iters = 0;
         for (;;) {
           if (!lu_valid) {
-            factor<LT>(c, cc);
+            factor(c, cc);
             lu_valid = true;
           }
-          conv = newton<LT>(c, cc, &iters);
+          conv = newton(c, cc, &iters);
           c.st.newton_iters += iters;
           if (conv || jac_current) break;
           jacobian(n, c.kap, s.yp, c.g, c.Jv);
@@ -1013,12 +1073,12 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
   __syncthreads();
 }
 
-template <typename LT>
+template <typename LT, bool GM>
 __global__ void __launch_bounds__(NT, 1) solve_kernel(const SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_cell;
   Smem s;
-  layout(a.net.S, a.net.R, a.net.nseg, sizeof(LT) == 4, smem_raw, &s);
+  layout(a.net.S, a.net.R, a.net.nseg, sizeof(LT) == 4, GM, smem_raw, &s);
   double* ws = a.ws + (size_t)blockIdx.x * a.ws_stride;
   for (;;) {
     if (threadIdx.x == 0) s_cell = atomicAdd(a.counter, 1);
@@ -1026,39 +1086,47 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(const SolveArgs a) {
     const int cell = s_cell;
     __syncthreads();
     if (cell >= a.C) break;
-    solve_cell<LT>(a, cell, s, ws);
+    solve_cell<LT, GM>(a, cell, s, ws);
   }
 }
 
-int launch_solver(const SolveArgs& a, bool mixed, int grid, void* stream) {
-  const size_t sm = smem_bytes(a.net.S, a.net.R, a.net.nseg, mixed);
-  cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e;
-  if (mixed) {
-    e = cudaFuncSetAttribute(solve_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    solve_kernel<float><<<grid, NT, sm, st>>>(a);
-  } else {
-    e = cudaFuncSetAttribute(solve_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    solve_kernel<double><<<grid, NT, sm, st>>>(a);
-  }
+template <typename LT, bool GM>
+static int launch_t(const SolveArgs& a, size_t sm, int grid, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(solve_kernel<LT, GM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  solve_kernel<LT, GM><<<grid, NT, sm, st>>>(a);
   return cudaGetLastError();
 }
 
-int solver_occupancy(int S, int R, int nseg, bool mixed) {
-  const size_t sm = smem_bytes(S, R, nseg, mixed);
-  if (S > 32 * kMaxColRegs || sm > device_smem_optin()) return 0;
+template <typename LT, bool GM>
+static int occupancy_t(size_t sm) {
   int blocks = 0;
-  cudaError_t e;
-  if (mixed) {
-    e = cudaFuncSetAttribute(solve_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, solve_kernel<float>, NT, sm);
-  } else {
-    e = cudaFuncSetAttribute(solve_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, solve_kernel<double>, NT, sm);
-  }
+  cudaError_t e = cudaFuncSetAttribute(solve_kernel<LT, GM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, solve_kernel<LT, GM>, NT, sm);
   return e == cudaSuccess ? blocks : 0;
+}
+
+SolverPlan plan_solver(int S, int R, int nseg, int nnzJ, bool mixed) {
+  SolverPlan p;
+  p.mixed = mixed;
+  const size_t optin = device_smem_optin();
+  // shared-memory matrix when it fits and the FP64 LU's register tiling allows (S <= 256)
+  p.gm = !(S <= 32 * kMaxColRegs && smem_bytes(S, R, nseg, mixed, false) <= optin);
+  p.smem = smem_bytes(S, R, nseg, mixed, p.gm);
+  p.ws_stride = workspace_doubles(S, R, nnzJ, mixed, p.gm);
+  p.occupancy = 0;
+  if (S > 2 * NT || p.smem > optin) return p;
+  if (mixed)
+    p.occupancy = p.gm ? occupancy_t<float, true>(p.smem) : occupancy_t<float, false>(p.smem);
+  else
+    p.occupancy = p.gm ? occupancy_t<double, true>(p.smem) : occupancy_t<double, false>(p.smem);
+  return p;
+}
+
+int launch_solver(const SolveArgs& a, const SolverPlan& p, int grid, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (p.mixed) return p.gm ? launch_t<float, true>(a, p.smem, grid, st) : launch_t<float, false>(a, p.smem, grid, st);
+  return p.gm ? launch_t<double, true>(a, p.smem, grid, st) : launch_t<double, false>(a, p.smem, grid, st);
 }
 
 int device_sm_count() {

@@ -133,3 +133,26 @@ def test_host_buffers_match_device(dev, net150):
     xh, sh, _ = carbox.solve_host(N, phi, x0, 0.0, 1e5 * YR)
     np.testing.assert_array_equal(xd, xh)
     np.testing.assert_array_equal(sd, sh)
+
+
+@pytest.fixture(scope="module")
+def net500():
+    return synth.make_network(500, 6000)
+
+
+@pytest.mark.parametrize("prec", [carbox.CBX_FP64, carbox.CBX_MIXED])
+def test_large_500_global_matrix(dev, net500, prec):
+    # 500 species: the Newton matrix does not fit in shared memory and lives in
+    # the CTA's global workspace (blocked LU for both precisions)
+    C = 6
+    phi = synth.cells(C, seed=3)
+    x0 = np.repeat(synth.initial_abundances(net500)[:, None], C, axis=1)
+    t_end = 1e5 * YR
+    N = carbox.Network.from_synth(net500)
+    x, st, _ = gpu_solve(N, phi, x0, t_end, dev, precision=prec)
+    assert np.all(st == carbox.CBX_CELL_OK)
+    for c in range(C):
+        assert_conserved(net500, x0[:, c], x[:, c])
+    for c in [0, C - 1]:
+        ref = bdf.solve_cell(net500, phi[c], x0[:, c], 0.0, t_end, 1e-4, 1e-20)
+        assert_twin(x[:, c], ref.x, f"500-species cell {c}")
