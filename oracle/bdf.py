@@ -109,6 +109,16 @@ def _newton_binomial(s, j):
     return v
 
 
+def rescale_matrix(q, rho):
+    """T[k-1, j-1], k, j = 1..q: the map of rescale_differences below."""
+    T = np.zeros((q, q))
+    for k in range(1, q + 1):
+        for j in range(1, q + 1):
+            T[k - 1, j - 1] = sum(((-1) ** i) * math.comb(k, i) * _newton_binomial(-i * rho, j)
+                                  for i in range(k + 1))
+    return T
+
+
 def rescale_differences(D, q, rho):
     """Replace D[1..q] (spacing h) by the differences of the same polynomial on spacing rho*h.
 
@@ -121,12 +131,7 @@ def rescale_differences(D, q, rho):
     than evaluating P and re-differencing) keeps y_n out of the arithmetic: the
     conserved sums e^T D[j], j >= 1, then stay at rounding level.
     """
-    T = np.zeros((q, q))
-    for k in range(1, q + 1):
-        for j in range(1, q + 1):
-            T[k - 1, j - 1] = sum(((-1) ** i) * math.comb(k, i) * _newton_binomial(-i * rho, j)
-                                  for i in range(k + 1))
-    D[1:q + 1] = T @ D[1:q + 1]
+    D[1:q + 1] = rescale_matrix(q, rho) @ D[1:q + 1]
 
 
 def newton_corrector(fun, t_new, y_pred, c, psi, lu, scale, tol, maxiter=NEWTON_MAXITER):
@@ -170,7 +175,7 @@ def integrate(fun, jac, t0, y0, t_end, rtol, atol, max_steps=100000, record=Fals
 
     Returns a Result with y(t_end), the status, counters, and (record=True) the
     program of difference-array operations that an exact replay needs:
-    ("init", h0), ("rescale", q, rho) and ("step", q, h, t_new) in order.
+    ("init", h0), ("rescale", q, rho) and ("step", q, h, t_new, y_new) in order.
     """
     S = y0.size
     stats = dict(steps=0, attempts=0, error_fails=0, newton_fails=0, rhs=0, jac=0, lu=0,
@@ -254,7 +259,7 @@ def integrate(fun, jac, t0, y0, t_end, rtol, atol, max_steps=100000, record=Fals
         # accepted step: update the differences to the new point
         stats["steps"] += 1
         if record:
-            program.append(("step", q, h, t_new))
+            program.append(("step", q, h, t_new, y_new.copy()))
         t = t_new
         jac_current = False
         n_equal += 1
