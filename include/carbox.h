@@ -60,6 +60,7 @@ extern "C" {
 #define CBX_CELL_MAX_STEPS 1    /* max_steps step attempts used */
 #define CBX_CELL_H_UNDERFLOW 2  /* step size fell below 10 ulp(t) */
 #define CBX_CELL_BAD_INPUT 5    /* non-finite or non-physical cell parameters */
+#define CBX_CELL_TAPE_FULL 6    /* solved, but the trajectory did not fit the tape (no gradient) */
 
 /* reaction types (Sec. 2 and App. B.1) */
 #define CBX_TWO_BODY 0    /* A + B -> products, k = alpha (T/300)^beta exp(-gamma/T) */
@@ -130,6 +131,7 @@ typedef struct {
 } cbx_netinfo;
 
 typedef struct cbx_network cbx_network;
+typedef struct cbx_tape cbx_tape;
 
 /* Version of this ABI (CBX_VERSION). */
 int cbx_version(void);
@@ -188,6 +190,60 @@ int cbx_solve(cbx_network* net, const cbx_cell_params* phi, const double* x0, in
 int cbx_solve_host(cbx_network* net, const cbx_cell_params* phi, const double* x0, int C, double t0,
                    double t_end, const cbx_options* opt, void* stream, double* x_out,
                    int* cell_status, cbx_cell_stats* stats);
+
+/*
+ * Replace the alpha parameters of all reactions (host pointer, R values) in the
+ * network, on the host and on its device. Synchronous. Used to differentiate
+ * with respect to ln alpha (Sec. 3: sensitivity to rate coefficients).
+ */
+int cbx_network_set_alpha(cbx_network* net, const double* alpha);
+
+/*
+ * Trajectory tape for the adjoint (Sec. 3: gradients of model outputs with
+ * respect to chemical and physical inputs; the paper obtains them by automatic
+ * differentiation of its solver, here a hand-written discrete adjoint of the
+ * BDF map is used).
+ * A tape holds, for up to C cells, the program of difference-array operations
+ * of the forward solve (initial step, every step-size/order rescale, every
+ * accepted step with its result y), plus copies of the cell parameters and
+ * initial abundances: the whole forward trajectory is checkpointed, one state
+ * per accepted step, so the reverse sweep needs no recomputation.
+ *   max_steps: accepted steps a cell may record (cells beyond it end with
+ *   CBX_CELL_TAPE_FULL). Device memory: C * (max_steps * (8 S + 2 * 16) + ...).
+ * Library-owned; free with cbx_tape_destroy.
+ */
+int cbx_tape_create(cbx_network* net, int C, int max_steps, cbx_tape** out);
+int cbx_tape_destroy(cbx_tape* tape);
+
+/*
+ * cbx_solve that also records the trajectory into `tape` (same arguments as
+ * cbx_solve; C must not exceed the tape's capacity). The tape remembers phi,
+ * x0, t0 and t_end for cbx_grad.
+ */
+int cbx_solve_record(cbx_network* net, const cbx_cell_params* phi, const double* x0, int C, double t0,
+                     double t_end, const cbx_options* opt, void* stream, double* x_out, int* cell_status,
+                     cbx_cell_stats* stats, cbx_tape* tape);
+
+/*
+ * Discrete adjoint (FP64) of the recorded solve: for the cotangent
+ * cot_x = dL/dx(t_end) (device [S][C]) it returns, on `stream`,
+ *   g_logalpha [R]  dL/d ln alpha_j summed over cells (device; deterministic order),
+ *   g_lognH   [C]  dL/d ln n_H per cell (device),
+ *   g_T       [C]  dL/dT per cell, T in K (device).
+ * Step sizes and orders are those of the recorded forward solve; each
+ * corrector is differentiated as if solved exactly. Cells whose status was
+ * not CBX_CELL_OK get zero gradients. Any output pointer may be NULL.
+ */
+int cbx_grad(cbx_tape* tape, const double* cot_x, void* stream, double* g_logalpha, double* g_lognH,
+             double* g_T);
+
+/*
+ * Read the recorded program of one cell to the host (for checks): kinds
+ * (0 init, 1 rescale, 2 step), orders q and values (h0, rho or h); at most cap
+ * entries. Returns the number of ops (>= 0) or a negative error code.
+ * Synchronises the device.
+ */
+int cbx_tape_program(const cbx_tape* tape, int cell, int* kinds, int* qs, double* values, int cap);
 
 /*
  * cbx_solve for callers that cannot allocate GPU memory while they run. The

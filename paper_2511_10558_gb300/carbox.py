@@ -17,6 +17,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "lib
 CBX_OK = 0
 CBX_E_ARG, CBX_E_CUDA, CBX_E_NOMEM, CBX_E_TOO_LARGE = -1, -2, -3, -4
 CBX_CELL_OK, CBX_CELL_MAX_STEPS, CBX_CELL_H_UNDERFLOW, CBX_CELL_BAD_INPUT = 0, 1, 2, 5
+CBX_CELL_TAPE_FULL = 6
 CBX_TWO_BODY, CBX_COSMIC_RAY, CBX_PHOTO = 0, 1, 2
 CBX_FP64, CBX_MIXED = 0, 1
 
@@ -90,6 +91,13 @@ def _load():
         "cbx_solve": (C.c_int, [P, P, P, C.c_int, C.c_double, C.c_double, C.POINTER(cbx_options), P, P, P, P]),
         "cbx_solve_host": (C.c_int, [P, P, P, C.c_int, C.c_double, C.c_double, C.POINTER(cbx_options), P, P,
                                      P, P]),
+        "cbx_network_set_alpha": (C.c_int, [P, P]),
+        "cbx_tape_create": (C.c_int, [P, C.c_int, C.c_int, C.POINTER(P)]),
+        "cbx_tape_destroy": (C.c_int, [P]),
+        "cbx_solve_record": (C.c_int, [P, P, P, C.c_int, C.c_double, C.c_double, C.POINTER(cbx_options), P, P, P,
+                                       P, P]),
+        "cbx_grad": (C.c_int, [P, P, P, P, P, P]),
+        "cbx_tape_program": (C.c_int, [P, C.c_int, P, P, P, C.c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -144,6 +152,11 @@ class Network:
     @classmethod
     def from_synth(cls, net):
         return cls(net.composition, net.charge, net.rtype, net.reac, net.prod, net.alpha, net.beta, net.gamma)
+
+    def set_alpha(self, alpha):
+        a = np.ascontiguousarray(alpha, dtype=np.float64)
+        assert a.shape == (self.R,)
+        check(lib.cbx_network_set_alpha(self.handle, a.ctypes.data_as(C.c_void_p)), "cbx_network_set_alpha")
 
     def info(self):
         inf = cbx_netinfo()
@@ -211,3 +224,114 @@ def solve_host(net, phi, x0, t0, t_end, opt=None, stream=None, want_stats=False)
                              status.ctypes.data_as(C.c_void_p),
                              stats.ctypes.data_as(C.c_void_p) if stats is not None else None), "cbx_solve_host")
     return x_out, status, stats
+
+
+class Tape:
+    """Owns a cbx_tape: the recorded forward trajectory of up to C cells."""
+
+    def __init__(self, net, n_cells, max_steps=2000):
+        h = C.c_void_p()
+        check(lib.cbx_tape_create(net.handle, int(n_cells), int(max_steps), C.byref(h)), "cbx_tape_create")
+        self.handle = h
+        self.net = net
+        self.C = n_cells
+
+    def program(self, cell, cap=100000):
+        """The recorded ops of one cell: list of (kind, q, value); kind 0 init, 1 rescale, 2 step."""
+        kinds = np.zeros(cap, np.int32)
+        qs = np.zeros(cap, np.int32)
+        vals = np.zeros(cap)
+        n = lib.cbx_tape_program(self.handle, int(cell), kinds.ctypes.data_as(C.c_void_p),
+                                 qs.ctypes.data_as(C.c_void_p), vals.ctypes.data_as(C.c_void_p), cap)
+        if n < 0:
+            raise CarboxError(n, "cbx_tape_program")
+        return [(int(kinds[i]), int(qs[i]), float(vals[i])) for i in range(min(n, cap))]
+
+    def close(self):
+        if self.handle:
+            lib.cbx_tape_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_record(net, tape, phi, x0, t0, t_end, opt=None, stream=None, stats=None):
+    """cbx_solve_record on torch CUDA tensors (as ``solve``), recording into ``tape``."""
+    import torch
+    Cn = phi.shape[0]
+    assert phi.is_cuda and phi.dtype == torch.float64 and phi.is_contiguous() and phi.shape[1] == 5
+    assert x0.is_cuda and x0.dtype == torch.float64 and x0.is_contiguous() and tuple(x0.shape) == (net.S, Cn)
+    if stats is not None:
+        assert stats.dtype == torch.int32 and stats.is_contiguous() and tuple(stats.shape) == (Cn, STATS_INTS)
+    x_out = torch.empty((net.S, Cn), dtype=torch.float64, device=phi.device)
+    status = torch.empty(Cn, dtype=torch.int32, device=phi.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(phi.device)
+    o = opt if opt is not None else options()
+    check(lib.cbx_solve_record(net.handle, _ptr(phi), _ptr(x0), Cn, float(t0), float(t_end), C.byref(o),
+                               C.c_void_p(stream.cuda_stream), _ptr(x_out), _ptr(status), _ptr(stats),
+                               tape.handle), "cbx_solve_record")
+    return x_out, status
+
+
+def grad(tape, cot_x, n_cells, stream=None):
+    """cbx_grad: (dL/d ln alpha [R], dL/d ln n_H [C], dL/dT [C]) for dL/dx(t_end) = cot_x [S, C]."""
+    import torch
+    assert cot_x.is_cuda and cot_x.dtype == torch.float64 and cot_x.is_contiguous()
+    dev = cot_x.device
+    ga = torch.empty(tape.net.R, dtype=torch.float64, device=dev)
+    gn = torch.empty(n_cells, dtype=torch.float64, device=dev)
+    gt = torch.empty(n_cells, dtype=torch.float64, device=dev)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    check(lib.cbx_grad(tape.handle, _ptr(cot_x), C.c_void_p(stream.cuda_stream), _ptr(ga), _ptr(gn), _ptr(gt)),
+          "cbx_grad")
+    return ga, gn, gt
+
+
+def _make_function():
+    import torch
+
+    class CellSolve(torch.autograd.Function):
+        """log10 x(t_end) [S, C] as a function of (ln alpha [R], ln n_H [C], T [C]).
+
+        Forward: cbx_network_set_alpha + cbx_solve_record (FP64 or mixed, per
+        ``opt``); backward: cbx_grad, the hand-written discrete adjoint.
+        Other inputs (x0, A_V, G0, zeta, times) are constants.
+        """
+
+        @staticmethod
+        def forward(ctx, log_alpha, log_nH, T, net, x0, av_g0_zeta, t_end, opt, max_steps):
+            net.set_alpha(torch.exp(log_alpha.detach()).cpu().numpy())
+            phi = torch.stack([torch.exp(log_nH.detach()), T.detach(), av_g0_zeta[:, 0], av_g0_zeta[:, 1],
+                               av_g0_zeta[:, 2]], dim=1).contiguous()
+            tape = Tape(net, phi.shape[0], max_steps)
+            x, status = solve_record(net, tape, phi, x0, 0.0, t_end, opt)
+            ctx.tape, ctx.x, ctx.status = tape, x, status
+            return torch.log10(x)
+
+        @staticmethod
+        def backward(ctx, g):
+            x = ctx.x
+            g = g.contiguous()
+            cot = torch.where(g != 0, g / (x * np.log(10.0)), torch.zeros_like(g)).contiguous()
+            ga, gn, gt = grad(ctx.tape, cot, x.shape[1])
+            return ga, gn, gt, None, None, None, None, None, None
+
+    return CellSolve
+
+
+_cell_solve = None
+
+
+def cell_solve(log_alpha, log_nH, T, net, x0, av_g0_zeta, t_end, opt=None, max_steps=2000):
+    """Differentiable solve: returns log10 x(t_end) [S, C] (see CellSolve)."""
+    global _cell_solve
+    if _cell_solve is None:
+        _cell_solve = _make_function()
+    return _cell_solve.apply(log_alpha, log_nH, T, net, x0, av_g0_zeta, t_end,
+                             opt if opt is not None else options(), max_steps)

@@ -4,6 +4,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -60,7 +61,8 @@ int upload(cbx_network* n) {
          o_sps = pk.add(h.spec_seg), o_ent = pk.add(h.rhs_ent), o_jrow = pk.add(h.jrow),
          o_jcol = pk.add(h.jcol), o_jrp = pk.add(h.jrow_ptr), o_jtp = pk.add(h.jterm_ptr),
          o_jt = pk.add(h.jterm), o_plp = pk.add(h.piv_lptr), o_pl = pk.add(h.piv_l),
-         o_pup = pk.add(h.piv_uptr), o_pu = pk.add(h.piv_u), o_perm = pk.add(h.perm);
+         o_pup = pk.add(h.piv_uptr), o_pu = pk.add(h.piv_u), o_perm = pk.add(h.perm),
+         o_rprod = pk.add(h.rprod);
   cudaGetDevice(&n->device);
   cudaError_t e = cudaMalloc(&n->dbuf, pk.bytes.size());
   if (e != cudaSuccess) {
@@ -99,10 +101,22 @@ int upload(cbx_network* n) {
   d.piv_uptr = (const int*)(b + o_pup);
   d.piv_u = (const int*)(b + o_pu);
   d.perm = (const int*)(b + o_perm);
+  d.rprod = (const int*)(b + o_rprod);
   return CBX_OK;
 }
 
 }  // namespace
+
+struct cbx_tape {
+  cbx_network* net = nullptr;
+  int C = 0, S = 0;
+  TapeDev dev;
+  void* dbuf = nullptr;
+  cbx_cell_params* phi = nullptr;  // [C] copy of the recorded solve's parameters
+  double* x0 = nullptr;            // [S][C] copy of its initial abundances
+  int* status = nullptr;           // [C] its cell status
+  int recorded_C = 0;
+};
 
 namespace cbx {
 // Record an error message for cbx_last_error() from another translation unit.
@@ -173,9 +187,11 @@ int cbx_network_info(const cbx_network* net, cbx_netinfo* out) {
   return CBX_OK;
 }
 
-int cbx_solve(cbx_network* net, const cbx_cell_params* phi, const double* x0, int C, double t0,
-              double t_end, const cbx_options* opt, void* stream, double* x_out, int* cell_status,
-              cbx_cell_stats* stats) {
+}  // extern "C"
+
+static int solve_impl(cbx_network* net, const cbx_cell_params* phi, const double* x0, int C, double t0,
+                      double t_end, const cbx_options* opt, void* stream, double* x_out, int* cell_status,
+                      cbx_cell_stats* stats, cbx_tape* tape) {
   if (!net) return fail(CBX_E_ARG, "net is NULL");
   if (C < 0) return fail(CBX_E_ARG, "C must be >= 0");
   if (C > 0 && (!phi || !x0 || !x_out || !cell_status)) return fail(CBX_E_ARG, "NULL array with C > 0");
@@ -221,6 +237,7 @@ int cbx_solve(cbx_network* net, const cbx_cell_params* phi, const double* x0, in
   a.x_out = x_out;
   a.status = cell_status;
   a.stats = stats;
+  if (tape) a.tape = tape->dev;
   a.ws_stride = plan.ws_stride;
   const size_t ws_bytes = (size_t)grid * a.ws_stride * sizeof(double) + 256;
   void* ws = nullptr;
@@ -233,7 +250,24 @@ int cbx_solve(cbx_network* net, const cbx_cell_params* phi, const double* x0, in
   cudaError_t e2 = cudaFreeAsync(ws, st);
   if (e != cudaSuccess) return cuda_fail(e, "solver launch");
   if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync(workspace)");
+  if (tape) {
+    e = cudaMemcpyAsync(tape->phi, phi, C * sizeof(cbx_cell_params), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(tape->x0, x0, (size_t)h.S * C * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tape->status, cell_status, C * sizeof(int), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(tape copies)");
+    tape->recorded_C = C;
+  }
   return CBX_OK;
+}
+
+
+extern "C" {
+
+int cbx_solve(cbx_network* net, const cbx_cell_params* phi, const double* x0, int C, double t0,
+              double t_end, const cbx_options* opt, void* stream, double* x_out, int* cell_status,
+              cbx_cell_stats* stats) {
+  return solve_impl(net, phi, x0, C, t0, t_end, opt, stream, x_out, cell_status, stats, nullptr);
 }
 
 int cbx_solve_host(cbx_network* net, const cbx_cell_params* phi, const double* x0, int C, double t0,
@@ -272,6 +306,141 @@ int cbx_solve_host(cbx_network* net, const cbx_cell_params* phi, const double* x
   e = cudaStreamSynchronize(st);
   if (rc == CBX_OK && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
   return rc;
+}
+
+int cbx_network_set_alpha(cbx_network* net, const double* alpha) {
+  if (!net || (!alpha && net->host.R > 0)) return fail(CBX_E_ARG, "NULL argument");
+  for (int j = 0; j < net->host.R; ++j)
+    if (!(alpha[j] == alpha[j])) return fail(CBX_E_ARG, "alpha has a NaN");
+  std::lock_guard<std::mutex> lock(net->mu);
+  for (int j = 0; j < net->host.R; ++j) net->host.alpha[j] = alpha[j];
+  if (net->dbuf && net->host.R > 0) {
+    cudaError_t e = cudaMemcpy((void*)net->dev.alpha, alpha, net->host.R * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(alpha)");
+  }
+  return CBX_OK;
+}
+
+int cbx_tape_create(cbx_network* net, int C, int max_steps, cbx_tape** out) {
+  if (!net || !out) return fail(CBX_E_ARG, "NULL argument");
+  *out = nullptr;
+  if (C < 1 || max_steps < 1) return fail(CBX_E_ARG, "need C >= 1 and max_steps >= 1");
+  int rc = upload(net);
+  if (rc) return rc;
+  cbx_tape* t = new (std::nothrow) cbx_tape();
+  if (!t) return fail(CBX_E_NOMEM, "host allocation failed");
+  t->net = net;
+  t->C = C;
+  t->S = net->host.S;
+  t->dev.cap_steps = max_steps;
+  t->dev.cap_ops = 4 * max_steps + 16;
+  const size_t n_ops = (size_t)C * t->dev.cap_ops;
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t o_nops = 0, o_kq = o_nops + al(C * 4), o_v = o_kq + al(n_ops * 4), o_y = o_v + al(n_ops * 8),
+               o_phi = o_y + al((size_t)C * max_steps * t->S * 8), o_x0 = o_phi + al(C * sizeof(cbx_cell_params)),
+               o_st = o_x0 + al((size_t)t->S * C * 8), total = o_st + al(C * 4);
+  cudaError_t e = cudaMalloc(&t->dbuf, total);
+  if (e != cudaSuccess) {
+    delete t;
+    return cuda_fail(e, "cudaMalloc(tape)");
+  }
+  char* b = (char*)t->dbuf;
+  t->dev.nops = (int*)(b + o_nops);
+  t->dev.ops_kq = (int*)(b + o_kq);
+  t->dev.ops_v = (double*)(b + o_v);
+  t->dev.ys = (double*)(b + o_y);
+  t->phi = (cbx_cell_params*)(b + o_phi);
+  t->x0 = (double*)(b + o_x0);
+  t->status = (int*)(b + o_st);
+  e = cudaMemset(t->dev.nops, 0, C * sizeof(int));
+  if (e != cudaSuccess) {
+    cudaFree(t->dbuf);
+    delete t;
+    return cuda_fail(e, "cudaMemset(tape)");
+  }
+  *out = t;
+  return CBX_OK;
+}
+
+int cbx_tape_destroy(cbx_tape* tape) {
+  if (!tape) return CBX_OK;
+  if (tape->dbuf) cudaFree(tape->dbuf);
+  delete tape;
+  return CBX_OK;
+}
+
+int cbx_solve_record(cbx_network* net, const cbx_cell_params* phi, const double* x0, int C, double t0,
+                     double t_end, const cbx_options* opt, void* stream, double* x_out, int* cell_status,
+                     cbx_cell_stats* stats, cbx_tape* tape) {
+  if (!tape) return fail(CBX_E_ARG, "tape is NULL");
+  if (tape->net != net) return fail(CBX_E_ARG, "the tape belongs to another network");
+  if (C > tape->C) return fail(CBX_E_ARG, "C exceeds the tape's capacity");
+  return solve_impl(net, phi, x0, C, t0, t_end, opt, stream, x_out, cell_status, stats, tape);
+}
+
+int cbx_grad(cbx_tape* tape, const double* cot_x, void* stream, double* g_logalpha, double* g_lognH,
+             double* g_T) {
+  if (!tape) return fail(CBX_E_ARG, "tape is NULL");
+  const int C = tape->recorded_C;
+  if (C < 1) return fail(CBX_E_ARG, "nothing recorded on this tape");
+  if (!cot_x) return fail(CBX_E_ARG, "cot_x is NULL");
+  cbx_network* net = tape->net;
+  const HostNet& h = net->host;
+  const int occ = grad_occupancy(h.S, h.R, h.nseg);
+  if (occ < 1) return fail(CBX_E_TOO_LARGE, "the adjoint supports networks whose FP64 matrix fits in shared memory");
+  const int grid = std::min(C, occ * device_sm_count());
+  cudaStream_t st = (cudaStream_t)stream;
+  GradArgs a{};
+  a.net = net->dev;
+  a.tape = tape->dev;
+  a.phi = tape->phi;
+  a.status = tape->status;
+  a.x0 = tape->x0;
+  a.cot = cot_x;
+  a.C = C;
+  for (int q = 0; q < kMaxOrder + 2; ++q) {
+    double g = 0.0;
+    for (int j = 1; j <= q; ++j) g += 1.0 / j;
+    a.gam[q] = g;
+  }
+  a.g_lognH = g_lognH;
+  a.g_T = g_T;
+  a.ws_stride = grad_workspace_doubles(h.S, h.R, h.nnzJ);
+  const size_t b_gcell = ((size_t)C * h.R * 8 + 255) & ~size_t(255);
+  const size_t b_ws = (size_t)grid * a.ws_stride * 8;
+  char* buf = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&buf, b_gcell + b_ws + 256, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(adjoint workspace)");
+  a.gcell = (double*)buf;
+  a.ws = (double*)(buf + b_gcell);
+  a.counter = (int*)(buf + b_gcell + b_ws);
+  e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = (cudaError_t)launch_grad(a, grid, stream);
+  if (e == cudaSuccess && g_logalpha) e = (cudaError_t)launch_reduce_cells(a.gcell, C, h.R, g_logalpha, stream);
+  cudaError_t e2 = cudaFreeAsync(buf, st);
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync(adjoint workspace)");
+  return CBX_OK;
+}
+
+int cbx_tape_program(const cbx_tape* tape, int cell, int* kinds, int* qs, double* values, int cap) {
+  if (!tape || cell < 0 || cell >= tape->C || cap < 0) return fail(CBX_E_ARG, "bad argument");
+  int n = 0;
+  cudaError_t e = cudaMemcpy(&n, tape->dev.nops + cell, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(tape)");
+  const int m = std::min(n, cap);
+  if (m > 0) {
+    std::vector<int> kq(m);
+    e = cudaMemcpy(kq.data(), tape->dev.ops_kq + (size_t)cell * tape->dev.cap_ops, m * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && values)
+      e = cudaMemcpy(values, tape->dev.ops_v + (size_t)cell * tape->dev.cap_ops, m * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(tape)");
+    for (int i = 0; i < m; ++i) {
+      if (kinds) kinds[i] = kq[i] >> 8;
+      if (qs) qs[i] = kq[i] & 255;
+    }
+  }
+  return n;
 }
 
 }  // extern "C"

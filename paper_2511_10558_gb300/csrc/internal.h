@@ -39,13 +39,26 @@ struct DevNet {
   const int* piv_uptr;   // [S+1] range of columns j > k with U(k,j) structurally non-zero
   const int* piv_u;
   const int* perm;       // [S] internal -> user species index
+  const int* rprod;      // [4R] products of each reaction (internal), -1 absent
 };
+
+// Forward trajectory recorded for the adjoint: per cell the program of
+// difference-array operations and the result y of every accepted step.
+struct TapeDev {
+  int cap_ops = 0, cap_steps = 0;
+  int* nops = nullptr;     // [C] ops recorded
+  int* ops_kq = nullptr;   // [C][cap_ops] (kind << 8) | q; kind 0 init, 1 rescale, 2 step
+  double* ops_v = nullptr; // [C][cap_ops] h0 (init), rho (rescale), h (step)
+  double* ys = nullptr;    // [C][cap_steps][S] step results, internal species order
+};
+
+enum { kOpInit = 0, kOpRescale = 1, kOpStep = 2 };
 
 // Host-side compiled network.
 struct HostNet {
   int S = 0, R = 0, nnzJ = 0, nnzLU = 0, nseg = 0, kdense = 0;
   double lu_flops = 0;
-  std::vector<int> perm, iperm;
+  std::vector<int> perm, iperm, rprod;
   std::vector<int> rtype, ra, rb;
   std::vector<double> alpha, beta, gamma;
   std::vector<int> seg_ptr, spec_seg, rhs_ent;
@@ -71,10 +84,34 @@ struct SolveArgs {
   double* x_out;
   int* status;
   cbx_cell_stats* stats;
+  TapeDev tape;    // recording target (tape.nops == nullptr: no recording)
   double* ws;      // per-CTA workspace, ws_stride doubles per CTA
   long long ws_stride;
   int* counter;    // next-cell counter, zero before the launch
 };
+
+struct GradArgs {
+  DevNet net;
+  TapeDev tape;
+  const cbx_cell_params* phi;  // [C] as recorded
+  const int* status;           // [C] forward status
+  const double* x0;            // [S][C] as recorded (user order)
+  const double* cot;           // [S][C] dL/dx(t_end) (user order)
+  int C;
+  double gam[kMaxOrder + 2];
+  double* gcell;               // [C][R] per-cell dL/d ln alpha
+  double* g_lognH;             // [C] or null
+  double* g_T;                 // [C] or null
+  double* ws;                  // per-CTA workspace, ws_stride doubles per CTA
+  long long ws_stride;
+  int* counter;
+};
+
+// Adjoint launch: workspace doubles per CTA, CTAs per SM, launch.
+long long grad_workspace_doubles(int S, int R, int nnzJ);
+int grad_occupancy(int S, int R, int nseg);
+int launch_grad(const GradArgs& a, int grid, void* stream);
+int launch_reduce_cells(const double* gcell, int C, int R, double* out, void* stream);
 
 // Launch plan of the solver kernel for one network and precision: matrix in
 // shared memory (gm = false) or in the CTA's global workspace (gm = true).

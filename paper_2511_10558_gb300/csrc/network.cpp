@@ -127,7 +127,9 @@ std::string compile_network(const cbx_species* sp, int S, const cbx_reaction* rx
   n.alpha.resize(R);
   n.beta.resize(R);
   n.gamma.resize(R);
+  n.rprod.assign((size_t)4 * R, -1);
   for (int j = 0; j < R; ++j) {
+    for (int p = 0; p < 4; ++p) n.rprod[4 * j + p] = rx[j].prod[p] >= 0 ? n.iperm[rx[j].prod[p]] : -1;
     n.rtype[j] = rx[j].type;
     n.ra[j] = n.iperm[rx[j].reac[0]];
     n.rb[j] = rx[j].reac[1] >= 0 ? n.iperm[rx[j].reac[1]] : -1;

@@ -914,6 +914,38 @@ __device__ bool newton(Cell<LT, GM>& c, double cc, int* iters) {
   return conv;
 }
 
+// Trajectory recorder (all threads keep identical counters; thread 0 writes ops).
+struct Recorder {
+  bool on = false, full = false;
+  int nops = 0, nsteps = 0;
+};
+
+__device__ void rec_op(const SolveArgs& a, int cell, Recorder& r, int kind, int q, double v) {
+  if (!r.on || r.full) return;
+  if (r.nops >= a.tape.cap_ops) {
+    r.full = true;
+    return;
+  }
+  if (threadIdx.x == 0) {
+    const size_t o = (size_t)cell * a.tape.cap_ops + r.nops;
+    a.tape.ops_kq[o] = (kind << 8) | q;
+    a.tape.ops_v[o] = v;
+  }
+  r.nops++;
+}
+
+__device__ void rec_step(const SolveArgs& a, int cell, Recorder& r, int q, double h, const double* y, int S) {
+  if (!r.on || r.full) return;
+  if (r.nops >= a.tape.cap_ops || r.nsteps >= a.tape.cap_steps) {
+    r.full = true;
+    return;
+  }
+  double* dst = a.tape.ys + ((size_t)cell * a.tape.cap_steps + r.nsteps) * S;
+  for (int i = threadIdx.x; i < S; i += NT) dst[i] = y[i];
+  rec_op(a, cell, r, kOpStep, q, h);
+  r.nsteps++;
+}
+
 template <typename LT, bool GM>
 __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
   const DevNet& n = a.net;
@@ -924,6 +956,8 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
   c.st.t_begin_ns = (long long)globaltimer();
   const cbx_cell_params p = a.phi[cell];
   int status = CBX_CELL_OK;
+  Recorder rec;
+  rec.on = a.tape.nops != nullptr;
   for (int i = threadIdx.x; i < S; i += NT) s.y[i] = a.x0[(size_t)__ldg(n.perm + i) * a.C + cell];
   if (!(p.n_H > 0.0) || !(p.T > 0.0) || !isfinite(p.n_H) || !isfinite(p.T) || !isfinite(p.A_V) ||
       !isfinite(p.G0) || !isfinite(p.zeta)) {
@@ -959,6 +993,7 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
       D[S + i] = h * s.f[i];
       for (int r = 2; r < kDiffRows; ++r) D[r * S + i] = 0.0;
     }
+    rec_op(a, cell, rec, kOpInit, 1, h);
     jacobian(n, c.kap, s.y, c.g, c.Jv);
     c.st.jac_evals++;
     int q = 1, n_equal = 0;
@@ -981,6 +1016,7 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
         if (t_new > t_end) {
           t_new = t_end;
           rescale(D, S, q, (t_end - t) / h, s.Tm);
+          rec_op(a, cell, rec, kOpRescale, q, (t_end - t) / h);
           n_equal = 0;
           lu_valid = false;
           h = t_end - t;
@@ -1015,6 +1051,7 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
         if (!conv) {
           c.st.newton_fails++;
           rescale(D, S, q, 0.5, s.Tm);
+          rec_op(a, cell, rec, kOpRescale, q, 0.5);
           h *= 0.5;
           n_equal = 0;
           lu_valid = false;
@@ -1027,6 +1064,7 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
           c.st.error_fails++;
           const double fac = fmax(0.2, 0.9 * uniform_pow(err, -1.0 / (q + 1), slot));
           rescale(D, S, q, fac, s.Tm);
+          rec_op(a, cell, rec, kOpRescale, q, fac);
           h *= fac;
           n_equal = 0;
           lu_valid = false;
@@ -1035,6 +1073,7 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
         accepted = true;
       }
       if (!accepted) break;
+      rec_step(a, cell, rec, q, h, s.y, S);
       c.st.steps++;
       t = t_new;
       jac_current = false;
@@ -1059,13 +1098,16 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
       q += best - 1;
       const double fac = fmin(10.0, 0.9 * fc[best]);
       rescale(D, S, q, fac, s.Tm);
+      rec_op(a, cell, rec, kOpRescale, q, fac);
       h *= fac;
       n_equal = 0;
       lu_valid = false;
     }
     for (int i = threadIdx.x; i < S; i += NT) a.x_out[(size_t)__ldg(n.perm + i) * a.C + cell] = D[i];
   }
+  if (rec.on && rec.full && status == CBX_CELL_OK) status = CBX_CELL_TAPE_FULL;
   if (threadIdx.x == 0) {
+    if (rec.on) a.tape.nops[cell] = rec.nops;
     a.status[cell] = status;
     c.st.t_end_ns = (long long)globaltimer();
     if (a.stats) a.stats[cell] = c.st;
@@ -1127,6 +1169,291 @@ int launch_solver(const SolveArgs& a, const SolverPlan& p, int grid, void* strea
   cudaStream_t st = (cudaStream_t)stream;
   if (p.mixed) return p.gm ? launch_t<float, true>(a, p.smem, grid, st) : launch_t<float, false>(a, p.smem, grid, st);
   return p.gm ? launch_t<double, true>(a, p.smem, grid, st) : launch_t<double, false>(a, p.smem, grid, st);
+}
+
+
+// ---------------------------------------------------------------- adjoint
+//
+// Discrete adjoint of the BDF map recorded on a tape (Sec. 3: sensitivities of
+// model outputs to chemical and physical inputs). For the frozen program
+// (init, rescales, accepted steps with their results y) and each corrector
+// differentiated as if solved exactly, the reverse sweep carries the cotangent
+// Lam of the difference array:
+//   step (q, h):  lam_d = sum_{i<=q+2} Lam'[i];  mu = (I - cJ(y))^{-T} lam_d
+//                 Lam[k] = sum_{i<=k} Lam'[i] + mu - lam_d - [k>=1] gamma_k/gamma_q mu  (k<=q)
+//                 Lam[q+1] = -Lam'[q+2], Lam[q+2] = 0
+//                 dL/d ln alpha_j += c (nu^T mu)_j r_j(y)   (c = h/gamma_q)
+//   rescale:      Lam[1..q] <- T(rho)^T Lam[1..q]
+//   init (h0):    dL/d ln alpha_j += h0 (nu^T Lam[1])_j r_j(y0)
+// ln n_H and T enter through the two-body coefficients: d ln kappa_j / d ln n_H
+// = 1 and d ln kappa_j / dT = beta_j/T + gamma_j/T^2.
+
+// v <- U^{-T} v (U unit upper, so U^T is unit lower), blocks of 32.
+__device__ void forwardT_crout64(const double* M, int S, double* v) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, ld = lead_dim(S);
+  for (int kb = 0; kb < S; kb += 32) {
+    const int nb = min(32, S - kb), ke = kb + nb;
+    if (w == 0) {
+      double val = lane < nb ? v[kb + lane] : 0.0;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        if (c < nb) {
+          const double yc = __shfl_sync(FULL, val, c);
+          if (lane > c && lane < nb) val = fma(-M[(kb + c) * ld + kb + lane], yc, val);
+        }
+      }
+      if (lane < nb) v[kb + lane] = val;
+    }
+    __syncthreads();
+    for (int i = ke + threadIdx.x; i < S; i += NT) {
+      double p0 = v[i], p1 = 0.0;
+      int c = 0;
+      for (; c + 2 <= nb; c += 2) {
+        p0 = fma(-M[(kb + c) * ld + i], v[kb + c], p0);
+        p1 = fma(-M[(kb + c + 1) * ld + i], v[kb + c + 1], p1);
+      }
+      if (c < nb) p0 = fma(-M[(kb + c) * ld + i], v[kb + c], p0);
+      v[i] = p0 + p1;
+    }
+    __syncthreads();
+  }
+}
+
+// v <- L^{-T} v (L unit lower, so L^T is unit upper), blocks of 32 from the bottom.
+__device__ void backwardT_crout64(const double* M, int S, double* v) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, ld = lead_dim(S);
+  for (int kb = ((S - 1) / 32) * 32; kb >= 0; kb -= 32) {
+    const int nb = min(32, S - kb);
+    if (w == 0) {
+      double val = lane < nb ? v[kb + lane] : 0.0;
+#pragma unroll
+      for (int c = 31; c >= 0; --c) {
+        if (c < nb) {
+          const double xc = __shfl_sync(FULL, val, c);
+          if (lane < c) val = fma(-M[(kb + c) * ld + kb + lane], xc, val);
+        }
+      }
+      if (lane < nb) v[kb + lane] = val;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kb; i += NT) {
+      double p0 = v[i], p1 = 0.0;
+      int c = 0;
+      for (; c + 2 <= nb; c += 2) {
+        p0 = fma(-M[(kb + c) * ld + i], v[kb + c], p0);
+        p1 = fma(-M[(kb + c + 1) * ld + i], v[kb + c + 1], p1);
+      }
+      if (c < nb) p0 = fma(-M[(kb + c) * ld + i], v[kb + c], p0);
+      v[i] = p0 + p1;
+    }
+    __syncthreads();
+  }
+}
+
+// w_j = (nu^T u)_j = sum over products of u - sum over reactants of u
+__device__ void nu_transpose(const DevNet& n, const double* u, double* w) {
+  for (int j = threadIdx.x; j < n.R; j += NT) {
+    const int b = n.rb[j];
+    double v = -u[n.ra[j]];
+    if (b >= 0) v -= u[b];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int pr = n.rprod[4 * j + p];
+      if (pr >= 0) v += u[pr];
+    }
+    w[j] = v;
+  }
+  __syncthreads();
+}
+
+// grow[j] += scale w_j r_j(y); returns the n_H and T contributions (block sums).
+__device__ void grad_accumulate(const DevNet& n, const double* kap, const double* dlnk_dT, const double* y,
+                                const double* w, double scale, double* grow, double* red, double* out_nH,
+                                double* out_T) {
+  double pn = 0.0, pt = 0.0;
+  for (int j = threadIdx.x; j < n.R; j += NT) {
+    const int b = n.rb[j];
+    double r = kap[j] * y[n.ra[j]];
+    if (b >= 0) r *= y[b];
+    const double c = scale * w[j] * r;
+    grow[j] += c;
+    if (n.rtype[j] == CBX_TWO_BODY) {
+      pn += c;
+      pt = fma(c, dlnk_dT[j], pt);
+    }
+  }
+  *out_nH += block_sum(pn, red);
+  *out_T += block_sum(pt, red);
+}
+
+__global__ void __launch_bounds__(NT, 1) grad_kernel(const GradArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_cell;
+  const DevNet& n = a.net;
+  const int S = n.S, R = n.R;
+  Smem s;
+  layout(S, R, n.nseg, false, false, smem_raw, &s);
+  double* M = (double*)s.M;
+  double* invd = (double*)s.invd;
+  double* Lam = s.D;
+  double* ws = a.ws + (size_t)blockIdx.x * a.ws_stride;
+  double* kap = ws;            // [R]
+  double* g = ws + R;          // [2R] partials, then nu^T mu
+  double* Jv = ws + 3 * R;     // [nnzJ]
+  double* dT = Jv + n.nnzJ;    // [R]
+  for (;;) {
+    if (threadIdx.x == 0) s_cell = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int cell = s_cell;
+    __syncthreads();
+    if (cell >= a.C) break;
+    double* grow = a.gcell + (size_t)cell * R;
+    for (int j = threadIdx.x; j < R; j += NT) grow[j] = 0.0;
+    double gnH = 0.0, gT = 0.0;
+    const int nops = a.tape.nops[cell];
+    if (a.status[cell] == CBX_CELL_OK && nops > 0) {
+      const cbx_cell_params p = a.phi[cell];
+      rate_coefficients(n, p, kap);
+      for (int j = threadIdx.x; j < R; j += NT)
+        dT[j] = n.rtype[j] == CBX_TWO_BODY ? n.beta[j] / p.T + n.gamma[j] / (p.T * p.T) : 0.0;
+      for (int i = threadIdx.x; i < S; i += NT) {
+        const int u = __ldg(n.perm + i);
+        Lam[i] = a.cot[(size_t)u * a.C + cell];
+        for (int r = 1; r < kDiffRows; ++r) Lam[r * S + i] = 0.0;
+        s.tmp[i] = a.x0[(size_t)u * a.C + cell];  // y0, internal order
+      }
+      __syncthreads();
+      const int* kq = a.tape.ops_kq + (size_t)cell * a.tape.cap_ops;
+      const double* vv = a.tape.ops_v + (size_t)cell * a.tape.cap_ops;
+      int sidx = 0;
+      for (int o = 0; o < nops; ++o) sidx += (kq[o] >> 8) == kOpStep;
+      for (int o = nops - 1; o >= 0; --o) {
+        const int kind = kq[o] >> 8, q = kq[o] & 255;
+        const double v = vv[o];
+        if (kind == kOpStep) {
+          --sidx;
+          const double* y = a.tape.ys + ((size_t)cell * a.tape.cap_steps + sidx) * S;
+          for (int i = threadIdx.x; i < S; i += NT) {
+            s.y[i] = y[i];
+            double L[kDiffRows];
+#pragma unroll
+            for (int r = 0; r < kDiffRows; ++r) L[r] = Lam[r * S + i];
+            double lam_d = 0.0;
+#pragma unroll
+            for (int r = 0; r < kDiffRows; ++r)
+              if (r <= q + 2) lam_d += L[r];
+            s.dv[i] = lam_d;
+            double pre = 0.0;
+#pragma unroll
+            for (int r = 0; r <= kMaxOrder; ++r) {
+              if (r <= q) {
+                pre += L[r];
+                Lam[r * S + i] = pre;
+              }
+            }
+            Lam[(q + 1) * S + i] = -L[q + 2 < kDiffRows ? q + 2 : kDiffRows - 1];
+            if (q + 2 < kDiffRows) Lam[(q + 2) * S + i] = 0.0;
+            s.dy[i] = lam_d;
+          }
+          __syncthreads();
+          const double c = v / a.gam[q];
+          jacobian(n, kap, s.y, g, Jv);
+          build_matrix<double>(n, Jv, c, M);
+          lu_crout64(n, M, invd);
+          forwardT_crout64(M, S, s.dy);
+          for (int i = threadIdx.x; i < S; i += NT) s.dy[i] *= invd[i];
+          __syncthreads();
+          backwardT_crout64(M, S, s.dy);
+          const double gq = a.gam[q];
+          for (int i = threadIdx.x; i < S; i += NT) {
+            const double mu = s.dy[i], md = mu - s.dv[i];
+            for (int r = 0; r <= q; ++r) {
+              double x = Lam[r * S + i] + md;
+              if (r >= 1) x -= a.gam[r] / gq * mu;
+              Lam[r * S + i] = x;
+            }
+          }
+          nu_transpose(n, s.dy, g);
+          grad_accumulate(n, kap, dT, s.y, g, c, grow, s.red, &gnH, &gT);
+        } else if (kind == kOpRescale) {
+          // Lam[1..q] <- T(rho)^T Lam[1..q]
+          if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            if (lane < q * q) {
+              const int k = lane / q + 1, j = lane % q + 1;
+              double acc = 0.0, binom = 1.0;
+              for (int i = 0; i <= k; ++i) {
+                const double sx = -i * v;
+                double nbv = 1.0;
+                for (int m = 0; m < j; ++m) nbv *= (sx + m) / (m + 1);
+                acc += ((i & 1) ? -binom : binom) * nbv;
+                binom = binom * (k - i) / (i + 1);
+              }
+              s.Tm[(k - 1) * kMaxOrder + (j - 1)] = acc;
+            }
+          }
+          __syncthreads();
+          for (int i = threadIdx.x; i < S; i += NT) {
+            double old[kMaxOrder];
+#pragma unroll
+            for (int k = 0; k < kMaxOrder; ++k) old[k] = k < q ? Lam[(k + 1) * S + i] : 0.0;
+            for (int j = 0; j < q; ++j) {
+              double acc = 0.0;
+#pragma unroll
+              for (int k = 0; k < kMaxOrder; ++k)
+                if (k < q) acc = fma(s.Tm[k * kMaxOrder + j], old[k], acc);
+              Lam[(j + 1) * S + i] = acc;
+            }
+          }
+          __syncthreads();
+        } else {  // init
+          nu_transpose(n, Lam + S, g);
+          grad_accumulate(n, kap, dT, s.tmp, g, v, grow, s.red, &gnH, &gT);
+        }
+      }
+    }
+    if (threadIdx.x == 0) {
+      if (a.g_lognH) a.g_lognH[cell] = gnH;
+      if (a.g_T) a.g_T[cell] = gT;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void reduce_cells_kernel(const double* gcell, int C, int R, double* out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= R) return;
+  double acc = 0.0;
+  for (int c = 0; c < C; ++c) acc += gcell[(size_t)c * R + j];
+  out[j] = acc;
+}
+
+long long grad_workspace_doubles(int S, int R, int nnzJ) {
+  (void)S;
+  return (4LL * R + nnzJ + 31) / 32 * 32;
+}
+
+int grad_occupancy(int S, int R, int nseg) {
+  const size_t sm = smem_bytes(S, R, nseg, false, false);
+  if (S > 32 * kMaxColRegs || sm > device_smem_optin()) return 0;
+  int blocks = 0;
+  cudaError_t e = cudaFuncSetAttribute(grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, grad_kernel, NT, sm);
+  return e == cudaSuccess ? blocks : 0;
+}
+
+int launch_grad(const GradArgs& a, int grid, void* stream) {
+  const size_t sm = smem_bytes(a.net.S, a.net.R, a.net.nseg, false, false);
+  cudaError_t e = cudaFuncSetAttribute(grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  grad_kernel<<<grid, NT, sm, (cudaStream_t)stream>>>(a);
+  return cudaGetLastError();
+}
+
+int launch_reduce_cells(const double* gcell, int C, int R, double* out, void* stream) {
+  if (R <= 0) return cudaSuccess;
+  reduce_cells_kernel<<<(R + 255) / 256, 256, 0, (cudaStream_t)stream>>>(gcell, C, R, out);
+  return cudaGetLastError();
 }
 
 int device_sm_count() {
