@@ -132,6 +132,7 @@ typedef struct {
 
 typedef struct cbx_network cbx_network;
 typedef struct cbx_tape cbx_tape;
+typedef struct cbx_server cbx_server;
 
 /* Version of this ABI (CBX_VERSION). */
 int cbx_version(void);
@@ -244,6 +245,33 @@ int cbx_grad(cbx_tape* tape, const double* cot_x, void* stream, double* g_logalp
  * Synchronises the device.
  */
 int cbx_tape_program(const cbx_tape* tape, int cell, int* kinds, int* qs, double* values, int cap);
+
+/*
+ * Continuous-batching request server (serving many 0-D cell solves of the
+ * Sec. 2 ODE for different networks). A scheduler thread admits submitted
+ * requests, in arrival order with smaller ones allowed past a head that does
+ * not fit, whenever one of `n_streams` CUDA streams and enough of the device
+ * memory budget `mem_budget` (bytes: inputs, outputs and solver workspace of
+ * the request) are free. Admitted requests run concurrently: each uses at most
+ * `max_ctas` persistent CTAs (0 = the whole device), which keep a cell's solver
+ * state on chip, retire it and back-fill from the request's remaining cells.
+ * Results are bitwise the same whatever else is in flight.
+ * Host arrays are copied at submit (phi [C], x0 [S][C]); cbx_server_wait
+ * blocks until the request is done and copies x_out [S][C] and cell_status [C]
+ * out (either may be NULL); times (3 doubles, may be NULL) receive the submit,
+ * start and completion times in seconds of a steady clock. A request's id is
+ * released by cbx_server_wait. cbx_server_poll gives its state (0 queued,
+ * 1 running, 2 done, 3 failed) and, when finished, its latency in seconds.
+ * cbx_server_destroy waits for running requests and drops queued ones.
+ * Errors: CBX_E_ARG, CBX_E_TOO_LARGE (request above the budget), CBX_E_CUDA.
+ */
+int cbx_server_create(size_t mem_budget, int n_streams, int max_ctas, cbx_server** out);
+int cbx_server_submit(cbx_server* server, cbx_network* net, const cbx_cell_params* phi, const double* x0, int C,
+                      double t0, double t_end, const cbx_options* opt, uint64_t* request_id);
+int cbx_server_poll(cbx_server* server, uint64_t request_id, int* state, double* latency_s);
+int cbx_server_wait(cbx_server* server, uint64_t request_id, double* x_out, int* cell_status, double* times);
+int cbx_server_stats(cbx_server* server, size_t* peak_bytes, int* peak_running, int* queued);
+int cbx_server_destroy(cbx_server* server);
 
 /*
  * cbx_solve for callers that cannot allocate GPU memory while they run. The

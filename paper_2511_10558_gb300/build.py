@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "lib", "libcarbox.so")
-SOURCES = ["solver.cu", "network.cpp", "capi.cpp", "noalloc.cu"]
+SOURCES = ["solver.cu", "network.cpp", "capi.cpp", "noalloc.cu", "server.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -98,6 +98,13 @@ def _load():
                                        P, P]),
         "cbx_grad": (C.c_int, [P, P, P, P, P, P]),
         "cbx_tape_program": (C.c_int, [P, C.c_int, P, P, P, C.c_int]),
+        "cbx_server_create": (C.c_int, [C.c_size_t, C.c_int, C.c_int, C.POINTER(P)]),
+        "cbx_server_submit": (C.c_int, [P, P, P, P, C.c_int, C.c_double, C.c_double, C.POINTER(cbx_options),
+                                        C.POINTER(C.c_uint64)]),
+        "cbx_server_poll": (C.c_int, [P, C.c_uint64, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+        "cbx_server_wait": (C.c_int, [P, C.c_uint64, P, P, P]),
+        "cbx_server_stats": (C.c_int, [P, C.POINTER(C.c_size_t), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "cbx_server_destroy": (C.c_int, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -335,3 +342,59 @@ def cell_solve(log_alpha, log_nH, T, net, x0, av_g0_zeta, t_end, opt=None, max_s
         _cell_solve = _make_function()
     return _cell_solve.apply(log_alpha, log_nH, T, net, x0, av_g0_zeta, t_end,
                              opt if opt is not None else options(), max_steps)
+
+
+class Server:
+    """cbx_server: continuous-batching solves of host-side requests."""
+
+    def __init__(self, mem_budget=8 << 30, n_streams=8, max_ctas=76):
+        h = C.c_void_p()
+        check(lib.cbx_server_create(int(mem_budget), int(n_streams), int(max_ctas), C.byref(h)), "cbx_server_create")
+        self.handle = h
+        self._nets = {}
+
+    def submit(self, net, phi, x0, t0, t_end, opt=None):
+        """phi [C, 5], x0 [S, C] numpy arrays; returns a request id."""
+        phi = np.ascontiguousarray(phi, dtype=np.float64)
+        x0 = np.ascontiguousarray(x0, dtype=np.float64)
+        rid = C.c_uint64()
+        o = opt if opt is not None else options()
+        check(lib.cbx_server_submit(self.handle, net.handle, phi.ctypes.data_as(C.c_void_p),
+                                    x0.ctypes.data_as(C.c_void_p), phi.shape[0], float(t0), float(t_end),
+                                    C.byref(o), C.byref(rid)), "cbx_server_submit")
+        self._nets[rid.value] = (net.S, phi.shape[0])
+        return rid.value
+
+    def poll(self, rid):
+        st = C.c_int()
+        lat = C.c_double()
+        check(lib.cbx_server_poll(self.handle, C.c_uint64(rid), C.byref(st), C.byref(lat)), "cbx_server_poll")
+        return st.value, lat.value
+
+    def wait(self, rid):
+        """Blocks; returns (x_out [S, C], status [C], (t_submit, t_start, t_done))."""
+        S, Cn = self._nets.pop(rid)
+        x = np.empty((S, Cn))
+        st = np.empty(Cn, dtype=np.int32)
+        t = np.empty(3)
+        check(lib.cbx_server_wait(self.handle, C.c_uint64(rid), x.ctypes.data_as(C.c_void_p),
+                                  st.ctypes.data_as(C.c_void_p), t.ctypes.data_as(C.c_void_p)), "cbx_server_wait")
+        return x, st, tuple(t)
+
+    def stats(self):
+        b = C.c_size_t()
+        r = C.c_int()
+        q = C.c_int()
+        check(lib.cbx_server_stats(self.handle, C.byref(b), C.byref(r), C.byref(q)), "cbx_server_stats")
+        return {"peak_bytes": b.value, "peak_running": r.value, "queued": q.value}
+
+    def close(self):
+        if self.handle:
+            lib.cbx_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

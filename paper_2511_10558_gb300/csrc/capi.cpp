@@ -121,6 +121,8 @@ struct cbx_tape {
 namespace cbx {
 // Record an error message for cbx_last_error() from another translation unit.
 int record_error(int code, const std::string& msg) { return fail(code, msg); }
+int solve_device(cbx_network* net, const cbx_cell_params* phi, const double* x0, int C, double t0, double t_end,
+                 const cbx_options* opt, void* stream, double* x_out, int* cell_status, int max_grid);
 }  // namespace cbx
 
 extern "C" {
@@ -191,7 +193,7 @@ int cbx_network_info(const cbx_network* net, cbx_netinfo* out) {
 
 static int solve_impl(cbx_network* net, const cbx_cell_params* phi, const double* x0, int C, double t0,
                       double t_end, const cbx_options* opt, void* stream, double* x_out, int* cell_status,
-                      cbx_cell_stats* stats, cbx_tape* tape) {
+                      cbx_cell_stats* stats, cbx_tape* tape, int max_grid = 0) {
   if (!net) return fail(CBX_E_ARG, "net is NULL");
   if (C < 0) return fail(CBX_E_ARG, "C must be >= 0");
   if (C > 0 && (!phi || !x0 || !x_out || !cell_status)) return fail(CBX_E_ARG, "NULL array with C > 0");
@@ -214,7 +216,8 @@ static int solve_impl(cbx_network* net, const cbx_cell_params* phi, const double
              h.S, h.R, plan.smem, 512, device_smem_optin());
     return fail(CBX_E_TOO_LARGE, m);
   }
-  const int grid = std::min(C, occ * device_sm_count());
+  int grid = std::min(C, occ * device_sm_count());
+  if (max_grid > 0) grid = std::min(grid, max_grid);
   cudaStream_t st = (cudaStream_t)stream;
   SolveArgs a{};
   a.net = net->dev;
@@ -444,3 +447,10 @@ int cbx_tape_program(const cbx_tape* tape, int cell, int* kinds, int* qs, double
 }
 
 }  // extern "C"
+
+namespace cbx {
+int solve_device(cbx_network* net, const cbx_cell_params* phi, const double* x0, int C, double t0, double t_end,
+                 const cbx_options* opt, void* stream, double* x_out, int* cell_status, int max_grid) {
+  return solve_impl(net, phi, x0, C, t0, t_end, opt, stream, x_out, cell_status, nullptr, nullptr, max_grid);
+}
+}  // namespace cbx

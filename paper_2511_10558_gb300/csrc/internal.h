@@ -127,6 +127,9 @@ SolverPlan plan_solver(int S, int R, int nseg, int nnzJ, bool mixed);
 // Launch the solver; returns a cudaError_t value.
 int launch_solver(const SolveArgs& a, const SolverPlan& p, int grid, void* stream);
 int device_sm_count();
+// cbx_solve on device buffers with at most max_grid CTAs (0: no cap).
+int solve_device(cbx_network* net, const cbx_cell_params* phi, const double* x0, int C, double t0, double t_end,
+                 const cbx_options* opt, void* stream, double* x_out, int* cell_status, int max_grid);
 // Set the calling thread's cbx_last_error() message; returns code.
 int record_error(int code, const std::string& msg);
 size_t device_smem_optin();
