@@ -283,6 +283,11 @@ def run_gpu(args):
     mixed_value = CELLS * len(msmx) / (sum(msmx) / 1e3)
     latmx = (stmx["t_end_ns"] - stmx["t_begin_ns"]) / 1e6
 
+    # ---- 500 species / 6000 reactions (matrix in the CTAs' global workspace)
+    large = None
+    if not args.no_large and ws == 1:
+        large = run_large_throughput(carbox, dev, stream, 4096, 608)
+
     # ---- end to end through the host-buffer C-ABI call (copies inside the timed region)
     opt = carbox.options(rtol=RTOL, atol=ATOL, precision=carbox.CBX_FP64)
     e2e_steps = max(1, min(args.steps, 2)) if not args.no_e2e else 0
@@ -329,6 +334,7 @@ def run_gpu(args):
                   "cells_ok": okmx, "cell_p50_ms": float(np.percentile(latmx, 50)),
                   "cell_p99_ms": float(np.percentile(latmx, 99)),
                   "mean_refine_sweeps_per_newton": float(stmx["refine_sweeps"].sum() / max(1, stmx["newton_iters"].sum()))},
+        "large_500": large,
         "counters_per_cell": {k: float(st64[k].mean()) for k in carbox.STATS_FIELDS},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
@@ -344,6 +350,216 @@ def run_gpu(args):
     print(json.dumps(line), flush=True)
 
 
+def _gpu_setup():
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    from paper_2511_10558_gb300 import build
+    build.build()
+    from paper_2511_10558_gb300 import carbox
+    return torch, dev, carbox
+
+
+def run_large_throughput(carbox, dev, stream, cells_mixed, cells_fp64):
+    """500 species / 6000 reactions, 1 Myr: mixed and FP64 cell-solves/s (one timed step each)."""
+    import torch
+    net = synth.make_network(500, 6000)
+    N = carbox.Network.from_synth(net)
+    out = {"workload": "500 species / 6000 reactions (seed 1500), 1 Myr, rtol 1e-4, atol 1e-20"}
+    for name, prec, C in [("mixed", carbox.CBX_MIXED, cells_mixed), ("fp64", carbox.CBX_FP64, cells_fp64)]:
+        phi = torch.tensor(synth.cells(C), device=dev)
+        x0 = torch.tensor(np.repeat(synth.initial_abundances(net)[:, None], C, axis=1), device=dev).contiguous()
+        st = carbox.stats_tensor(C, dev)
+        o = carbox.options(rtol=RTOL, atol=ATOL, precision=prec)
+        carbox.solve(N, phi[:152].contiguous(), x0[:, :152].contiguous(), 0.0, T_END, o, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, status, _ = carbox.solve(N, phi, x0, 0.0, T_END, o, stream=stream, stats=st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        sd = carbox.stats_dict(st.cpu().numpy())
+        lat = (sd["t_end_ns"] - sd["t_begin_ns"]) / 1e6
+        out[name] = {"cells": C, "ms": ms, "value": C / (ms / 1e3), "unit": "cell-solves/s",
+                     "cells_ok": int((status == 0).sum().item()), "cell_p50_ms": float(np.percentile(lat, 50)),
+                     "cell_p99_ms": float(np.percentile(lat, 99)),
+                     "steps_per_cell": float(sd["steps"].mean()), "lu_per_cell": float(sd["lu_factors"].mean())}
+    out["mixed_speedup_vs_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    return out
+
+
+def run_large(args):
+    """Config 3: 500 species, mixed vs FP64 throughput and per-species error vs the FP64 oracle."""
+    torch, dev, carbox = _gpu_setup()
+    from oracle import bdf, chem
+    stream = torch.cuda.current_stream(dev)
+    thr = run_large_throughput(carbox, dev, stream, 4096, 608)
+    net = synth.make_network(500, 6000)
+    N = carbox.Network.from_synth(net)
+    ns = args.ref_cells if args.ref_cells < 64 else 3
+    phi = synth.cells(4096)[:ns]
+    x0 = np.repeat(synth.initial_abundances(net)[:, None], ns, axis=1)
+    errs = {}
+    for name, prec in [("mixed", carbox.CBX_MIXED), ("fp64", carbox.CBX_FP64)]:
+        x, st, _ = carbox.solve_host(N, phi, x0, 0.0, T_END, carbox.options(rtol=RTOL, atol=ATOL, precision=prec))
+        errs[name] = (x, st)
+    rel = {"mixed": [], "fp64": []}
+    cons = {"mixed": 0.0, "fp64": 0.0}
+    E = np.vstack([net.composition.T, net.charge[None, :]]).astype(float)
+    for c in range(ns):
+        ref = bdf.solve_cell(net, phi[c], x0[:, c], 0.0, T_END, RTOL, ATOL)
+        big = ref.x > 1e-12
+        for name in rel:
+            x = errs[name][0][:, c]
+            rel[name].append(np.abs(x[big] / ref.x[big] - 1))
+            e0 = E @ x0[:, c]
+            dE = np.abs(E @ x - e0)
+            den = np.where(np.arange(E.shape[0]) == E.shape[0] - 1, np.abs(net.charge) @ x0[:, c], e0)
+            cons[name] = max(cons[name], float(np.max(dE / den)))
+    res = {"config": "large", "workload": thr["workload"], "throughput": thr, "oracle_cells": ns}
+    for name in rel:
+        r = np.concatenate(rel[name])
+        res["error_vs_fp64_oracle_" + name] = {"max": float(r.max()), "median": float(np.median(r)),
+                                               "p99": float(np.percentile(r, 99)),
+                                               "max_conservation_rel": cons[name]}
+    print(json.dumps(res), flush=True)
+
+
+def run_adjoint(args):
+    """Config 4: 150 sp, 1024 cells, 1e5 yr; forward (recorded) and adjoint times; gradient checks."""
+    torch, dev, carbox = _gpu_setup()
+    from oracle import adjoint as adj
+    from oracle import bdf
+    stream = torch.cuda.current_stream(dev)
+    net = synth.make_network(S_SP, R_RX)
+    N = carbox.Network.from_synth(net)
+    C = 1024
+    t_end = 1e5 * synth.YEAR
+    phi_h = synth.cells(C, seed=7)
+    x0_h = np.repeat(synth.initial_abundances(net)[:, None], C, axis=1)
+    phi = torch.tensor(phi_h, device=dev)
+    x0 = torch.tensor(x0_h, device=dev).contiguous()
+    tape = carbox.Tape(N, C, 2000)
+    o = carbox.options(rtol=RTOL, atol=ATOL, precision=carbox.CBX_FP64)
+    carbox.solve_record(N, tape, phi, x0, 0.0, t_end, o)   # warm-up
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record(stream)
+    x, st = carbox.solve_record(N, tape, phi, x0, 0.0, t_end, o)
+    e[1].record(stream)
+    torch.cuda.synchronize()
+    # loss: 10 seeded targets per cell (species above 1e-12 at t_f), targets +-0.5 dex
+    xh = x.cpu().numpy()
+    rng = np.random.default_rng(11)
+    cot = np.zeros_like(xh)
+    targets = []
+    for c in range(C):
+        cand = np.flatnonzero(xh[:, c] > 1e-12)
+        tg = np.sort(rng.choice(cand, size=min(10, len(cand)), replace=False))
+        yt = np.log10(xh[tg, c]) + rng.uniform(-0.5, 0.5, len(tg))
+        targets.append((tg, yt))
+        cot[:, c] = adj.log10_loss(xh[:, c], tg, yt)[1]
+    cot_d = torch.tensor(cot, device=dev).contiguous()
+    carbox.grad(tape, cot_d, C)  # warm-up
+    torch.cuda.synchronize()
+    e[2].record(stream)
+    ga, gn, gt = carbox.grad(tape, cot_d, C)
+    e[3].record(stream)
+    torch.cuda.synchronize()
+    fwd_ms, bwd_ms = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
+    gn_h, gt_h = gn.cpu().numpy(), gt.cpu().numpy()
+    # checks on sampled cells: oracle adjoint of the GPU program, and central FD (step 1e-6)
+    checks = []
+    for c in [0, 517]:
+        prog = []
+        for kind, q, v in tape.program(c):
+            prog.append(("init", v) if kind == 0 else ("rescale", q, v) if kind == 1 else ("step", q, v, 0.0, None))
+        tg, yt = targets[c]
+        xr, prog_r = adj.replay(net, phi_h[c], x0_h[:, c], prog)
+        _, cr = adj.log10_loss(xr, tg, yt)
+        g = adj.adjoint(net, phi_h[c], x0_h[:, c], prog_r, cr)
+        eps = 1e-6
+        pp, pm = phi_h[c].copy(), phi_h[c].copy()
+        pp[0] *= np.exp(eps)
+        pm[0] *= np.exp(-eps)
+        fd_nH = (adj.log10_loss(adj.replay(net, pp, x0_h[:, c], prog)[0], tg, yt)[0] -
+                 adj.log10_loss(adj.replay(net, pm, x0_h[:, c], prog)[0], tg, yt)[0]) / (2 * eps)
+        pp, pm = phi_h[c].copy(), phi_h[c].copy()
+        pp[1] += eps * phi_h[c, 1]
+        pm[1] -= eps * phi_h[c, 1]
+        fd_T = (adj.log10_loss(adj.replay(net, pp, x0_h[:, c], prog)[0], tg, yt)[0] -
+                adj.log10_loss(adj.replay(net, pm, x0_h[:, c], prog)[0], tg, yt)[0]) / (2 * eps * phi_h[c, 1])
+        checks.append({"cell": c, "rel_err_lnnH_vs_oracle_adjoint": abs(gn_h[c] / g[1] - 1),
+                       "rel_err_T_vs_oracle_adjoint": abs(gt_h[c] / g[2] - 1),
+                       "rel_err_lnnH_vs_fd": abs(gn_h[c] / fd_nH - 1), "rel_err_T_vs_fd": abs(gt_h[c] / fd_T - 1)})
+    res = {"config": "adjoint", "workload": f"{S_SP} species / {R_RX} reactions, {C} cells, 0 -> 1e5 yr, FP64, "
+                                             "loss = sum over 10 seeded targets of (log10 x - y)^2",
+           "forward_record_ms": fwd_ms, "adjoint_ms": bwd_ms, "backward_over_forward": bwd_ms / fwd_ms,
+           "cells_ok": int((st == 0).sum().item()), "gradients": "ln alpha [1500] summed over cells, ln n_H [1024], T [1024]",
+           "checks": checks}
+    print(json.dumps(res), flush=True)
+
+
+def run_serving(args):
+    """Config 5: Poisson requests over 32/150/500-species networks through cbx_server."""
+    torch, dev, carbox = _gpu_setup()
+    import threading
+    nets = {}
+    for S, R in [(32, 200), (150, 1500), (500, 6000)]:
+        net = synth.make_network(S, R)
+        nets[S] = (net, carbox.Network.from_synth(net))
+    rng = np.random.default_rng(13)
+    n_req = max(1, int(rng.poisson(args.rate * args.duration)))
+    arrivals = np.sort(rng.uniform(0.0, args.duration, n_req))
+    reqs = []
+    for k in range(n_req):
+        S = int(rng.choice([32, 150, 500]))
+        C = int(np.clip(np.round(np.exp(rng.uniform(0.0, np.log(4096.0)))), 1, 4096))
+        t_end = 10.0 ** rng.uniform(3.0, 7.0) * synth.YEAR
+        phi = synth.cells(C, seed=1000 + k)
+        x0 = np.repeat(synth.initial_abundances(nets[S][0])[:, None], C, axis=1)
+        reqs.append((arrivals[k], S, phi, x0, t_end))
+    opt = carbox.options(rtol=RTOL, atol=ATOL, precision=carbox.CBX_MIXED)
+    srv = carbox.Server(mem_budget=64 << 30, n_streams=8, max_ctas=76)
+    ids = [None] * n_req
+    t0 = time.perf_counter()
+
+    def submitter():
+        for k, (ta, S, phi, x0, t_end) in enumerate(reqs):
+            d = ta - (time.perf_counter() - t0)
+            if d > 0:
+                time.sleep(d)
+            ids[k] = srv.submit(nets[S][1], phi, x0, 0.0, t_end, opt)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    lat, cells, ok = [], 0, 0
+    for k in range(n_req):
+        x, st, (ts, tb, td) = srv.wait(ids[k])
+        lat.append(td - ts)
+        cells += len(st)
+        ok += int((st == 0).sum())
+    wall = time.perf_counter() - t0
+    stats = srv.stats()
+    srv.close()
+    lat = np.array(lat)
+    by = {}
+    for S in (32, 150, 500):
+        sel = np.array([r[1] == S for r in reqs])
+        if sel.any():
+            by[str(S)] = {"requests": int(sel.sum()), "p50_s": float(np.percentile(lat[sel], 50)),
+                          "p99_s": float(np.percentile(lat[sel], 99))}
+    res = {"config": "serving", "workload": f"Poisson arrivals at {args.rate}/s for {args.duration} s; networks "
+           "32/150/500 species uniform; cells log-uniform 1..4096; spans log-uniform 1e3..1e7 yr; mixed precision",
+           "requests": n_req, "cells": cells, "cells_ok": ok, "wall_s": wall,
+           "throughput_cells_per_s": cells / wall, "throughput_requests_per_s": n_req / wall,
+           "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+           "by_network": by, "server": {"mem_budget": 64 << 30, "streams": 8, "max_ctas": 76, **stats}}
+    print(json.dumps(res), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -355,9 +571,19 @@ def main():
     ap.add_argument("--cells", type=int, default=16384)
     ap.add_argument("--only", choices=["fp64", "mixed"], default=None)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--config", choices=["bench", "large", "adjoint", "serving"], default="bench")
+    ap.add_argument("--duration", type=float, default=2.0, help="serving: seconds of Poisson arrivals")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: mean requests per second")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "large":
+        run_large(args)
+    elif args.config == "adjoint":
+        run_adjoint(args)
+    elif args.config == "serving":
+        run_serving(args)
     else:
         run_gpu(args)
 
