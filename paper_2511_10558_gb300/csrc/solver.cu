@@ -125,14 +125,21 @@ __device__ void rhs(const DevNet& n, const double* __restrict__ kap, const doubl
   }
   __syncthreads();
   for (int s = threadIdx.x; s < n.nseg; s += NT) {
-    double acc = 0.0;
+    double acc0 = 0.0, acc1 = 0.0;
     const int e1 = __ldg(n.seg_ptr + s + 1);
-    for (int e = __ldg(n.seg_ptr + s); e < e1; ++e) {
-      const int t = __ldg(n.rhs_ent + e);
-      const double v = r[t >> 1];
-      acc += (t & 1) ? -v : v;
+    int e = __ldg(n.seg_ptr + s);
+    for (; e + 2 <= e1; e += 2) {
+      const int t0 = __ldg(n.rhs_ent + e), t1 = __ldg(n.rhs_ent + e + 1);
+      const double v0 = r[t0 >> 1], v1 = r[t1 >> 1];
+      acc0 += (t0 & 1) ? -v0 : v0;
+      acc1 += (t1 & 1) ? -v1 : v1;
     }
-    part[s] = acc;
+    if (e < e1) {
+      const int t0 = __ldg(n.rhs_ent + e);
+      const double v0 = r[t0 >> 1];
+      acc0 += (t0 & 1) ? -v0 : v0;
+    }
+    part[s] = acc0 + acc1;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < n.S; i += NT) {
@@ -482,6 +489,30 @@ template <typename LT, bool FULL>
 __device__ __forceinline__ void panel_u12(LT* M, int S, int ld, int kb, int nb) {
   const int ke = kb + nb, ncol = S - ke;
   const LT* L = M + kb * ld + kb;
+  if (ncol + nb <= NT) {
+    // one pass: threads < ncol take A12 columns, the next nb the identity
+    // columns; L11^{-1} is written over L11 after everyone has read it
+    const int t = threadIdx.x;
+    const bool a12 = t < ncol, ident = !a12 && t < ncol + nb;
+    const int col = ke + t, jj = t - ncol;
+    LT v[NB];
+#pragma unroll
+    for (int r = 0; r < NB; ++r)
+      v[r] = a12 && (FULL || r < nb) ? M[(kb + r) * ld + col] : (ident && r == jj ? LT(1) : LT(0));
+    if (a12 || ident) l11_solve<LT, FULL>(L, ld, nb, v);
+    __syncthreads();
+    if (a12) {
+#pragma unroll
+      for (int r = 0; r < NB; ++r)
+        if (FULL || r < nb) M[(kb + r) * ld + col] = v[r];
+    } else if (ident) {
+#pragma unroll
+      for (int r = 0; r < NB; ++r)
+        if (r > jj && (FULL || r < nb)) M[(kb + r) * ld + kb + jj] = v[r];
+    }
+    __syncthreads();
+    return;
+  }
   // U12 = L11^{-1} A12, one column per thread (A12 does not overlap L11)
   for (int t = threadIdx.x; t < ncol; t += NT) {
     const int col = ke + t;
@@ -591,6 +622,39 @@ __device__ __forceinline__ void trailing_update(LT* M, int S, int ld, int kb, in
   __syncthreads();
 }
 
+// U_bb^{-1} of every diagonal block, in place (strict upper part; the
+// diagonal reciprocals stay in invd): one warp per block, columns left to
+// right, X[0:j, j] = -X[0:j, 0:j] U[0:j, j] / U_jj with X[0:j, 0:j] (already
+// in place) and the still-original column j; lanes take the rows r < j.
+template <typename LT>
+__device__ void invert_upper_blocks(LT* M, const LT* invd, int S, int ld) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nblk = (S + NB - 1) / NB;
+  for (int b = warp; b < nblk; b += NW) {
+    const int kb = b * NB, nb = min(NB, S - kb);
+    LT* U = M + kb * ld + kb;
+    for (int j = 1; j < nb; ++j) {
+      LT acc = LT(0);
+      if (lane < j) {
+        LT a0 = invd[kb + lane] * U[lane * ld + j], a1 = LT(0), a2 = LT(0), a3 = LT(0);
+        int c = lane + 1;
+        for (; c + 4 <= j; c += 4) {
+          a0 += U[lane * ld + c] * U[c * ld + j];
+          a1 += U[lane * ld + c + 1] * U[(c + 1) * ld + j];
+          a2 += U[lane * ld + c + 2] * U[(c + 2) * ld + j];
+          a3 += U[lane * ld + c + 3] * U[(c + 3) * ld + j];
+        }
+        for (; c < j; ++c) a0 += U[lane * ld + c] * U[c * ld + j];
+        acc = (a0 + a1) + (a2 + a3);
+      }
+      __syncwarp();
+      if (lane < j) U[lane * ld + j] = -invd[kb + j] * acc;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
 // LARGE: networks of 257..512 species (matrix in global memory): two panel
 // rows per thread and up to 16 column groups in the trailing update.
 template <typename LT, bool LARGE>
@@ -608,33 +672,7 @@ __device__ void lu_blocked(LT* M, LT* invd, int S, int ld) {
     }
     trailing_update<LT, LARGE>(M, S, ld, kb, nb);
   }
-  // U_bb^{-1}: thread per column of each diagonal block, NT / NB blocks at a
-  // time; a chunk's reads finish before its writes
-  const int nblk = (S + NB - 1) / NB;
-  for (int b0 = 0; b0 < nblk; b0 += NT / NB) {
-    const int b = b0 + threadIdx.x / NB, jj = threadIdx.x % NB;
-    LT x[NB];
-    const bool act = b < nblk && b * NB + jj < S;
-    const int kb = b * NB;
-    if (act) {
-      const LT* U = M + kb * ld + kb;
-#pragma unroll
-      for (int r = NB - 1; r >= 0; --r) {
-        LT acc = r == jj ? LT(1) : LT(0);
-#pragma unroll
-        for (int c = r + 1; c < NB; ++c)
-          if (c <= jj) acc -= U[r * ld + c] * x[c];
-        x[r] = r <= jj ? acc * invd[kb + r] : LT(0);
-      }
-    }
-    __syncthreads();
-    if (act) {
-#pragma unroll
-      for (int r = 0; r < NB; ++r)
-        if (r < jj) M[(kb + r) * ld + kb + jj] = x[r];
-    }
-    __syncthreads();
-  }
+  invert_upper_blocks<LT>(M, invd, S, ld);
 }
 
 template <typename LT, bool FULL>
@@ -755,6 +793,26 @@ long long workspace_doubles(int S, int R, int nnzJ, bool mixed, bool gm) {
 
 // ---------------------------------------------------------------- BDF pieces
 
+// T[k][j](rho) = sum_{i=0..k} (-1)^i C(k,i) C(-i rho + j - 1, j), with
+// C(s + j - 1, j) = s (s+1) ... (s+j-1) / j!. Binomials and 1/j! come from
+// constant tables: no FP64 division (each costs ~10 FP64 instructions, and
+// this runs on one warp).
+__constant__ double c_inv_fact[kMaxOrder + 1] = {1.0, 1.0, 0.5, 1.0 / 6.0, 1.0 / 24.0, 1.0 / 120.0};
+__constant__ double c_binom[kMaxOrder + 1][kMaxOrder + 1] = {{1, 0, 0, 0, 0, 0}, {1, 1, 0, 0, 0, 0},
+                                                             {1, 2, 1, 0, 0, 0}, {1, 3, 3, 1, 0, 0},
+                                                             {1, 4, 6, 4, 1, 0}, {1, 5, 10, 10, 5, 1}};
+
+__device__ __forceinline__ double rescale_entry(int k, int j, double rho) {
+  double acc = 0.0;
+  for (int i = 0; i <= k; ++i) {
+    const double s = -i * rho;
+    double p = 1.0;
+    for (int m = 0; m < j; ++m) p *= s + m;
+    acc = fma((i & 1) ? -c_binom[k][i] : c_binom[k][i], p, acc);
+  }
+  return acc * c_inv_fact[j];
+}
+
 // D[1..q] <- T(rho) D[1..q], T[k][j] = sum_i (-1)^i C(k,i) C(-i rho + j - 1, j):
 // the differences of the interpolating polynomial on the new spacing. The
 // q x q matrix is computed by one warp (lane = (k, j)).
@@ -763,17 +821,7 @@ __device__ void rescale(double* D, int S, int q, double rho, double* Tm) {
     const int lane = threadIdx.x;
     if (lane < q * q) {
       const int k = lane / q + 1, j = lane % q + 1;
-      double acc = 0.0;
-      double binom = 1.0;  // C(k, i)
-      for (int i = 0; i <= k; ++i) {
-        const double s = -i * rho;
-        double nb = 1.0;
-        for (int m = 0; m < j; ++m) nb *= (s + m) / (m + 1);
-        const double term = ((i & 1) ? -binom : binom) * nb;
-        acc += term;
-        binom = binom * (k - i) / (i + 1);
-      }
-      Tm[(k - 1) * kMaxOrder + (j - 1)] = acc;
+      Tm[(k - 1) * kMaxOrder + (j - 1)] = rescale_entry(k, j, rho);
     }
   }
   __syncthreads();
@@ -802,7 +850,7 @@ struct Cell {
   double* kap;
   double* g;
   double* Jv;
-  cbx_cell_stats st;
+  cbx_cell_stats* st;  // shared-memory counters, updated by thread 0 only
 };
 
 // Solve (I - cJ) dy = w with the factored matrix in shared memory.
@@ -851,7 +899,7 @@ __device__ void linear_solve(Cell<float, GM>& c, double cc, const double* w, dou
       const double t = corr * c.s.wsc[i];
       sq = fma(t, t, sq);
     }
-    c.st.refine_sweeps++;
+    if (threadIdx.x == 0) c.st->refine_sweeps++;
     const double nrm = sqrt(block_sum(sq, c.s.red) / S);
     if (!(nrm > c.a.refine_tol)) break;
   }
@@ -868,7 +916,7 @@ __device__ void factor(Cell<LT, GM>& c, double cc) {
     else
       lu_crout64(c.n, c.M, (double*)c.s.invd);
   }
-  c.st.lu_factors++;
+  if (threadIdx.x == 0) c.st->lu_factors++;
 }
 
 // Simplified Newton on d - c f(yp + d) + psi = 0. Leaves y = yp + d, dv = d.
@@ -886,7 +934,7 @@ __device__ bool newton(Cell<LT, GM>& c, double cc, int* iters) {
   for (int k = 0; k < kNewtonMaxIter; ++k) {
     *iters = k + 1;
     rhs(c.n, c.kap, s.y, s.f, s.r, s.part);
-    c.st.rhs_evals++;
+    if (threadIdx.x == 0) c.st->rhs_evals++;
     int bad = 0;
     for (int i = threadIdx.x; i < S; i += NT) bad |= !isfinite(s.f[i]);
     if (__syncthreads_or(bad)) break;
@@ -952,8 +1000,13 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
   const int S = n.S;
   // workspace: kappa [R], partials [2R], J values [nnzJ], then (GM) the matrix
   LT* M = GM ? (LT*)(ws + (3LL * n.R + n.nnzJ + 31) / 32 * 32) : (LT*)s.M;
-  Cell<LT, GM> c{a, n, s, M, ws, ws + n.R, ws + 3 * n.R, {}};
-  c.st.t_begin_ns = (long long)globaltimer();
+  __shared__ cbx_cell_stats s_stats;
+  Cell<LT, GM> c{a, n, s, M, ws, ws + n.R, ws + 3 * n.R, &s_stats};
+  if (threadIdx.x == 0) {
+    *c.st = cbx_cell_stats{};
+    c.st->t_begin_ns = (long long)globaltimer();
+  }
+  int attempts = 0;
   const cbx_cell_params p = a.phi[cell];
   int status = CBX_CELL_OK;
   Recorder rec;
@@ -971,7 +1024,7 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
     double* D = s.D;
     // f0 and the initial step (Hairer, Norsett & Wanner I, II.4, p = 1)
     rhs(n, c.kap, s.y, s.f, s.r, s.part);
-    c.st.rhs_evals++;
+    if (threadIdx.x == 0) c.st->rhs_evals++;
     for (int i = threadIdx.x; i < S; i += NT) s.wsc[i] = 1.0 / (atol + rtol * fabs(s.y[i]));
     __syncthreads();
     const double d0 = wrms(s.y, s.wsc, 1.0, S, s.red);
@@ -980,7 +1033,7 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
     for (int i = threadIdx.x; i < S; i += NT) s.tmp[i] = s.y[i] + h0 * s.f[i];
     __syncthreads();
     rhs(n, c.kap, s.tmp, s.dy, s.r, s.part);
-    c.st.rhs_evals++;
+    if (threadIdx.x == 0) c.st->rhs_evals++;
     for (int i = threadIdx.x; i < S; i += NT) s.tmp[i] = s.dy[i] - s.f[i];
     __syncthreads();
     const double d2 = wrms(s.tmp, s.wsc, 1.0, S, s.red) / h0;
@@ -995,7 +1048,7 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
     }
     rec_op(a, cell, rec, kOpInit, 1, h);
     jacobian(n, c.kap, s.y, c.g, c.Jv);
-    c.st.jac_evals++;
+    if (threadIdx.x == 0) c.st->jac_evals++;
     int q = 1, n_equal = 0;
     bool jac_current = true, lu_valid = false;
     double* slot = s.red + 40;
@@ -1003,11 +1056,11 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
       bool accepted = false;
       double t_new = t, err = 0.0;
       while (!accepted) {
-        if (c.st.attempts >= a.max_steps) {
+        if (attempts >= a.max_steps) {
           status = CBX_CELL_MAX_STEPS;
           break;
         }
-        c.st.attempts++;
+        attempts++;
         if (h < 10.0 * (::nextafter(t, __longlong_as_double(0x7ff0000000000000LL)) - t)) {
           status = CBX_CELL_H_UNDERFLOW;
           break;
@@ -1041,15 +1094,15 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
             lu_valid = true;
           }
           conv = newton(c, cc, &iters);
-          c.st.newton_iters += iters;
+          if (threadIdx.x == 0) c.st->newton_iters += iters;
           if (conv || jac_current) break;
           jacobian(n, c.kap, s.yp, c.g, c.Jv);
-          c.st.jac_evals++;
+          if (threadIdx.x == 0) c.st->jac_evals++;
           jac_current = true;
           lu_valid = false;
         }
         if (!conv) {
-          c.st.newton_fails++;
+          if (threadIdx.x == 0) c.st->newton_fails++;
           rescale(D, S, q, 0.5, s.Tm);
           rec_op(a, cell, rec, kOpRescale, q, 0.5);
           h *= 0.5;
@@ -1061,7 +1114,7 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
         __syncthreads();
         err = wrms(s.dv, s.wsc, 1.0 / (q + 1), S, s.red);
         if (err > 1.0) {
-          c.st.error_fails++;
+          if (threadIdx.x == 0) c.st->error_fails++;
           const double fac = fmax(0.2, 0.9 * uniform_pow(err, -1.0 / (q + 1), slot));
           rescale(D, S, q, fac, s.Tm);
           rec_op(a, cell, rec, kOpRescale, q, fac);
@@ -1074,7 +1127,7 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
       }
       if (!accepted) break;
       rec_step(a, cell, rec, q, h, s.y, S);
-      c.st.steps++;
+      if (threadIdx.x == 0) c.st->steps++;
       t = t_new;
       jac_current = false;
       n_equal++;
@@ -1109,8 +1162,9 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
   if (threadIdx.x == 0) {
     if (rec.on) a.tape.nops[cell] = rec.nops;
     a.status[cell] = status;
-    c.st.t_end_ns = (long long)globaltimer();
-    if (a.stats) a.stats[cell] = c.st;
+    c.st->attempts = attempts;
+    c.st->t_end_ns = (long long)globaltimer();
+    if (a.stats) a.stats[cell] = *c.st;
   }
   __syncthreads();
 }
@@ -1381,15 +1435,7 @@ __global__ void __launch_bounds__(NT, 1) grad_kernel(const GradArgs a) {
             const int lane = threadIdx.x;
             if (lane < q * q) {
               const int k = lane / q + 1, j = lane % q + 1;
-              double acc = 0.0, binom = 1.0;
-              for (int i = 0; i <= k; ++i) {
-                const double sx = -i * v;
-                double nbv = 1.0;
-                for (int m = 0; m < j; ++m) nbv *= (sx + m) / (m + 1);
-                acc += ((i & 1) ? -binom : binom) * nbv;
-                binom = binom * (k - i) / (i + 1);
-              }
-              s.Tm[(k - 1) * kMaxOrder + (j - 1)] = acc;
+              s.Tm[(k - 1) * kMaxOrder + (j - 1)] = rescale_entry(k, j, v);
             }
           }
           __syncthreads();
