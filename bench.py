@@ -126,6 +126,27 @@ def flush_l2(buf):
     buf.add_(1.0)
 
 
+def shard_cells(global_phi, rank, per_rank):
+    """A rank's contiguous block of the global batch (weak scaling: per_rank cells each)."""
+    return np.ascontiguousarray(global_phi[rank * per_rank:(rank + 1) * per_rank])
+
+
+def max_over_ranks(seconds, device):
+    """The slowest rank's time: an all-reduce (MAX) when a process group is up."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return seconds
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(world, per_rank, steps, t_max):
+    """Whole-job cell-solves/s: every rank solved per_rank cells per step."""
+    return world * per_rank * steps / t_max
+
+
 # ------------------------------------------------------------------ oracle timing
 
 _NET_CACHE = {}
@@ -217,8 +238,7 @@ def run_gpu(args):
     R_two = int(np.sum(net.rtype == synth.TWO_BODY))
     R_one = net.n_reactions - R_two
     n_nu = int(sum(np.sum(net.reac >= 0, axis=1)) + sum(np.sum(net.prod >= 0, axis=1)))
-    allphi = synth.cells(CELLS * ws)
-    phi_h = np.ascontiguousarray(allphi[rank * CELLS:(rank + 1) * CELLS])
+    phi_h = shard_cells(synth.cells(CELLS * ws), rank, CELLS)
     x0_h = np.ascontiguousarray(np.repeat(synth.initial_abundances(net)[:, None], CELLS, axis=1))
     phi = torch.tensor(phi_h, device=dev)
     x0 = torch.tensor(x0_h, device=dev)
@@ -256,13 +276,8 @@ def run_gpu(args):
         ms64 = timed(carbox.CBX_FP64, args.steps, args.warmup) if args.only != "mixed" else [float("nan")]
     st64 = carbox.stats_dict(stats.cpu().numpy())
     ok64 = int((status == 0).sum().item())
-    t_local = sum(ms64) / 1e3
-    t_max = t_local
-    if ws > 1:
-        tt = torch.tensor([t_local], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = ws * CELLS * args.steps / t_max
+    t_max = max_over_ranks(sum(ms64) / 1e3, dev)
+    value = weak_value(ws, CELLS, args.steps, t_max)
     ms_per_step = 1e3 * t_max / args.steps
     lat = (st64["t_end_ns"] - st64["t_begin_ns"]) / 1e6
     fl = algorithmic_flops(info, st64, R_two, R_one, n_nu)
@@ -297,11 +312,7 @@ def run_gpu(args):
         xh, sh, _ = carbox.solve_host(N, phi_h, x0_h.reshape(S_SP, CELLS), 0.0, T_END, opt, stream=stream)
     barrier()
     e2e_t = max(time.perf_counter() - t0, 1e-9)
-    e2e_value = ws * CELLS * e2e_steps / e2e_t if ws == 1 and e2e_steps else None
-    if ws > 1:
-        tt = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_value = ws * CELLS * e2e_steps / float(tt.item())
+    e2e_value = weak_value(ws, CELLS, e2e_steps, max_over_ranks(e2e_t, dev)) if e2e_steps else None
 
     if rank != 0:
         return

@@ -37,9 +37,13 @@
 
 #include "internal.h"
 
+#ifndef CBX_THREADS
+#define CBX_THREADS 256
+#endif
+
 namespace cbx {
 
-constexpr int NT = 256;
+constexpr int NT = CBX_THREADS;  // threads per CTA
 constexpr int NW = NT / 32;
 constexpr int kNewtonMaxIter = 4;
 constexpr int kMaxColRegs = 8;  // columns per lane in the LU update: S <= 256
