@@ -59,8 +59,8 @@ int upload(cbx_network* n) {
   size_t o_rtype = pk.add(h.rtype), o_alpha = pk.add(h.alpha), o_beta = pk.add(h.beta),
          o_gamma = pk.add(h.gamma), o_ra = pk.add(h.ra), o_rb = pk.add(h.rb), o_seg = pk.add(h.seg_ptr),
          o_sps = pk.add(h.spec_seg), o_ent = pk.add(h.rhs_ent), o_jrow = pk.add(h.jrow),
-         o_jcol = pk.add(h.jcol), o_jrp = pk.add(h.jrow_ptr), o_jtp = pk.add(h.jterm_ptr),
-         o_jt = pk.add(h.jterm), o_plp = pk.add(h.piv_lptr), o_pl = pk.add(h.piv_l),
+         o_jcol = pk.add(h.jcol), o_jrp = pk.add(h.jrow_ptr), o_jgp = pk.add(h.jg_ptr),
+         o_jgs = pk.add(h.jg_slot), o_jgl = pk.add(h.jg_len), o_jgt = pk.add(h.jg_term), o_plp = pk.add(h.piv_lptr), o_pl = pk.add(h.piv_l),
          o_pup = pk.add(h.piv_uptr), o_pu = pk.add(h.piv_u), o_perm = pk.add(h.perm),
          o_rprod = pk.add(h.rprod);
   cudaGetDevice(&n->device);
@@ -94,8 +94,11 @@ int upload(cbx_network* n) {
   d.jrow = (const int*)(b + o_jrow);
   d.jcol = (const int*)(b + o_jcol);
   d.jrow_ptr = (const int*)(b + o_jrp);
-  d.jterm_ptr = (const int*)(b + o_jtp);
-  d.jterm = (const int*)(b + o_jt);
+  d.njg = h.njg;
+  d.jg_ptr = (const int*)(b + o_jgp);
+  d.jg_slot = (const int*)(b + o_jgs);
+  d.jg_len = (const int*)(b + o_jgl);
+  d.jg_term = (const int*)(b + o_jgt);
   d.piv_lptr = (const int*)(b + o_plp);
   d.piv_l = (const int*)(b + o_pl);
   d.piv_uptr = (const int*)(b + o_pup);

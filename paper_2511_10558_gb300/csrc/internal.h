@@ -32,8 +32,12 @@ struct DevNet {
   const int* jrow;       // [nnzJ] row of each Jacobian slot (slots sorted by row, col)
   const int* jcol;       // [nnzJ] column
   const int* jrow_ptr;   // [S+1] CSR row pointer over the slots
-  const int* jterm_ptr;  // [nnzJ+1] term range per slot
-  const int* jterm;      // ((2 reaction + reactant slot) << 1) | negative
+  int njg;               // Jacobian gather groups of 32 slots
+  const int* jg_ptr;     // [njg+1] term range of each group (a multiple of 32)
+  const int* jg_slot;    // [32 njg] slot of each (group, lane), -1 past nnzJ
+  const int* jg_len;     // [32 njg] terms of that slot
+  const int* jg_term;    // term e of (group g, lane l) at jg_ptr[g] + 32 e + l:
+                         // ((2 reaction + reactant slot) << 1) | negative
   const int* piv_lptr;   // [S+1] range of rows i > k with L(i,k) structurally non-zero
   const int* piv_l;
   const int* piv_uptr;   // [S+1] range of columns j > k with U(k,j) structurally non-zero
@@ -62,7 +66,9 @@ struct HostNet {
   std::vector<int> rtype, ra, rb;
   std::vector<double> alpha, beta, gamma;
   std::vector<int> seg_ptr, spec_seg, rhs_ent;
-  std::vector<int> jrow, jcol, jrow_ptr, jterm_ptr, jterm;
+  std::vector<int> jrow, jcol, jrow_ptr;
+  int njg = 0;
+  std::vector<int> jg_ptr, jg_slot, jg_len, jg_term;
   std::vector<int> piv_lptr, piv_l, piv_uptr, piv_u;
 };
 

@@ -185,10 +185,33 @@ std::string compile_network(const cbx_species* sp, int S, const cbx_reaction* rx
         for (int c = 0; c < std::abs(v); ++c) terms[sl].push_back(((2 * j + s) << 1) | (v < 0 ? 1 : 0));
       }
     }
-  n.jterm_ptr.push_back(0);
-  for (int s = 0; s < n.nnzJ; ++s) {
-    n.jterm.insert(n.jterm.end(), terms[s].begin(), terms[s].end());
-    n.jterm_ptr.push_back((int)n.jterm.size());
+  // Slots ordered by term count (longest first) and dealt in groups of 32,
+  // one group per warp pass; a group's terms are interleaved (term e of lane l
+  // at jg_ptr[g] + 32 e + l) so that the warp reads them coalesced and its
+  // lanes sum lists of similar length. Padding entries hold term 0 (a valid
+  // index that the device does not add).
+  std::vector<int> order(n.nnzJ);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return terms[a].size() > terms[b].size(); });
+  n.njg = (n.nnzJ + 31) / 32;
+  n.jg_ptr.push_back(0);
+  for (int g = 0; g < n.njg; ++g) {
+    int cnt = 0;
+    for (int l = 0; l < 32; ++l) {
+      const int idx = g * 32 + l;
+      const int s = idx < n.nnzJ ? order[idx] : -1;
+      const int len = s >= 0 ? (int)terms[s].size() : 0;
+      n.jg_slot.push_back(s);
+      n.jg_len.push_back(len);
+      cnt = std::max(cnt, len);
+    }
+    for (int e = 0; e < cnt; ++e)
+      for (int l = 0; l < 32; ++l) {
+        const int s = n.jg_slot[(size_t)g * 32 + l];
+        n.jg_term.push_back(s >= 0 && e < (int)terms[s].size() ? terms[s][e] : 0);
+      }
+    n.jg_ptr.push_back((int)n.jg_term.size());
   }
   // symbolic LU of the internal pattern
   std::vector<uint8_t> F(ip);

@@ -171,15 +171,33 @@ __device__ void jacobian(const DevNet& n, const double* __restrict__ kap, const 
     }
   }
   __syncthreads();
-  for (int s = threadIdx.x; s < n.nnzJ; s += NT) {
+  // one warp per group of 32 slots; each lane sums its slot's terms in list
+  // order (four loads ahead, one accumulator)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int gi = warp; gi < n.njg; gi += NW) {
+    const int s = __ldg(n.jg_slot + gi * 32 + lane);
+    const int len = __ldg(n.jg_len + gi * 32 + lane);
+    const int p0 = __ldg(n.jg_ptr + gi), cnt = (__ldg(n.jg_ptr + gi + 1) - p0) >> 5;
+    const int* tp = n.jg_term + p0 + lane;
     double acc = 0.0;
-    const int e1 = n.jterm_ptr[s + 1];
-    for (int e = n.jterm_ptr[s]; e < e1; ++e) {
-      const int t = n.jterm[e];
-      const double v = g[t >> 1];
-      acc += (t & 1) ? -v : v;
+    int e = 0;
+    for (; e + 4 <= cnt; e += 4) {
+      int t[4];
+      double v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) t[u] = __ldg(tp + 32 * (e + u));
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = g[t[u] >> 1];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (e + u < len) acc += (t[u] & 1) ? -v[u] : v[u];
     }
-    Jv[s] = acc;
+    for (; e < cnt; ++e) {
+      const int t = __ldg(tp + 32 * e);
+      const double v = g[t >> 1];
+      if (e < len) acc += (t & 1) ? -v : v;
+    }
+    if (s >= 0) Jv[s] = acc;
   }
   __syncthreads();
 }
@@ -229,8 +247,38 @@ __device__ void prep_pivot(const DevNet& n, double* M, double* invd, int k, int 
   }
 }
 
+// Rows r0 and (if two) r1 of L(:,k) minus their multiple of U(k,:), MC
+// column groups per lane.
+template <int MC>
+__device__ __forceinline__ void update_rows(double* r0, double* r1, bool two, int k, const int (&jc)[MC],
+                                            const double (&uv)[MC], int nu, int lane) {
+  const double a = r0[k], b = r1[k];
+  double x0[MC], x1[MC];
+#pragma unroll
+  for (int m = 0; m < MC; ++m) {
+    x0[m] = r0[jc[m]];
+    x1[m] = r1[jc[m]];
+  }
+#pragma unroll
+  for (int m = 0; m < MC; ++m) x0[m] = fma(-a, uv[m], x0[m]);
+  if (two) {
+#pragma unroll
+    for (int m = 0; m < MC; ++m) x1[m] = fma(-b, uv[m], x1[m]);
+  }
+#pragma unroll
+  for (int m = 0; m < MC; ++m) {
+    if (lane + 32 * m < nu) {
+      r0[jc[m]] = x0[m];
+      if (two) r1[jc[m]] = x1[m];
+    }
+  }
+}
+
 // All rows of L(:,k) assigned to this warp, with exactly MC column groups of
 // U(k,:) per lane (a predicated FP64 instruction still takes the FP64 pipe).
+// When row k+1 is in L(:,k), warp 0 updates it alone and prepares pivot k+1
+// (in the dense trailing block the scaling by 1/pivot is applied in registers
+// before the single store); the other warps take the other rows in pairs.
 template <int MC>
 __device__ __forceinline__ void crout_rows(const DevNet& n, double* M, double* invd, int k, int kd, bool dense,
                                            int l0, int l1, int u0, int nu, bool next_in_l) {
@@ -248,40 +296,36 @@ __device__ __forceinline__ void crout_rows(const DevNet& n, double* M, double* i
       uv[m] = M[k * ld + jc[m]];
     }
   }
-  // warp 0 takes row k+1 alone when it is in L(:,k) (then prepares pivot
-  // k+1); the other rows go to warps 1..NW-1, two at a time
-  const int first = next_in_l ? l0 + 1 : l0;
-  const int nw = next_in_l ? NW - 1 : NW;
-  const int wi = next_in_l ? w - 1 : w;
-  const bool row_next = next_in_l && w == 0;
-  for (int e = row_next ? l0 : first + wi; row_next ? e == l0 : e < l1; e += row_next ? 1 : 2 * nw) {
-    const bool two = !row_next && e + nw < l1;
-    double* r0 = M + lrow(n, dense, k, e) * ld;
-    double* r1 = two ? M + lrow(n, dense, k, e + nw) * ld : r0;
-    const double a = r0[k], b = r1[k];
-    double x0[MC], x1[MC];
+  if (next_in_l && w == 0) {
+    double* r0 = M + (k + 1) * ld;
+    const double a = r0[k];
+    double x0[MC];
 #pragma unroll
-    for (int m = 0; m < MC; ++m) {
-      x0[m] = r0[jc[m]];
-      x1[m] = r1[jc[m]];
-    }
+    for (int m = 0; m < MC; ++m) x0[m] = fma(-a, uv[m], r0[jc[m]]);
+    if (dense) {
+      // lane 0, group 0 holds the new diagonal (column k+1)
+      const double inv = __drcp_rn(__shfl_sync(FULL, x0[0], 0));
+      if (lane == 0) invd[k + 1] = inv;
 #pragma unroll
-    for (int m = 0; m < MC; ++m) x0[m] = fma(-a, uv[m], x0[m]);
-    if (two) {
+      for (int m = 0; m < MC; ++m)
+        if (lane + 32 * m < nu) r0[jc[m]] = jc[m] > k + 1 ? x0[m] * inv : x0[m];
+    } else {
 #pragma unroll
-      for (int m = 0; m < MC; ++m) x1[m] = fma(-b, uv[m], x1[m]);
-    }
-#pragma unroll
-    for (int m = 0; m < MC; ++m) {
-      if (lane + 32 * m < nu) {
-        r0[jc[m]] = x0[m];
-        if (two) r1[jc[m]] = x1[m];
-      }
-    }
-    if (row_next) {
+      for (int m = 0; m < MC; ++m)
+        if (lane + 32 * m < nu) r0[jc[m]] = x0[m];
       __syncwarp();
       prep_pivot(n, M, invd, k + 1, kd, lane);
     }
+    return;
+  }
+  const int first = next_in_l ? l0 + 1 : l0;
+  const int nw = next_in_l ? NW - 1 : NW;
+  const int wi = next_in_l ? w - 1 : w;
+  for (int e = first + wi; e < l1; e += 2 * nw) {
+    const bool two = e + nw < l1;
+    double* r0 = M + lrow(n, dense, k, e) * ld;
+    double* r1 = two ? M + lrow(n, dense, k, e + nw) * ld : r0;
+    update_rows<MC>(r0, r1, two, k, jc, uv, nu, lane);
   }
 }
 
