@@ -126,7 +126,8 @@ typedef struct {
   int nnz_lu;         /* non-zeros of the symbolic L + U fill (after ordering) */
   double lu_flops;    /* flops of one numeric LU on that fill */
   double lu_flops_dense; /* 2 S^3 / 3 */
-  int smem_bytes_fp64;   /* shared memory per CTA of the FP64 solver */
+  int smem_bytes_fp64;   /* shared memory per CTA of the FP64 solver (with the sparse
+                            pivots' index lists staged when they fit) */
   int smem_bytes_mixed;  /* shared memory per CTA of the mixed solver */
 } cbx_netinfo;
 

@@ -187,7 +187,7 @@ int cbx_network_info(const cbx_network* net, cbx_netinfo* out) {
   out->nnz_lu = h.nnzLU;
   out->lu_flops = h.lu_flops;
   out->lu_flops_dense = 2.0 * h.S * (double)h.S * h.S / 3.0;
-  out->smem_bytes_fp64 = (int)smem_bytes(h.S, h.R, h.nseg, false, false);
+  out->smem_bytes_fp64 = (int)smem_bytes(h.S, h.R, h.nseg, false, false, h.head_ints);
   out->smem_bytes_mixed = (int)smem_bytes(h.S, h.R, h.nseg, true, false);
   return CBX_OK;
 }
@@ -211,7 +211,7 @@ static int solve_impl(cbx_network* net, const cbx_cell_params* phi, const double
   if (rc) return rc;
   const HostNet& h = net->host;
   const bool mixed = o.precision == CBX_MIXED;
-  const SolverPlan plan = plan_solver(h.S, h.R, h.nseg, h.nnzJ, mixed);
+  const SolverPlan plan = plan_solver(h.S, h.R, h.nseg, h.nnzJ, mixed, h.head_ints);
   const int occ = plan.occupancy;
   if (occ < 1) {
     char m[200];

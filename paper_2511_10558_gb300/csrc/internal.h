@@ -19,7 +19,7 @@ constexpr int kSegLen = 16;            // entries per right-hand-side gather seg
 // (fill-reducing order); perm maps internal -> user index.
 struct DevNet {
   int S, R, nnzJ, nseg;
-  int kdense;            // pivots k >= kdense have a fully dense trailing block
+  int kdense;            // pivots k >= kdense are factored over the full index ranges
   const int* rtype;      // [R]
   const double* alpha;   // [R]
   const double* beta;    // [R]
@@ -61,6 +61,7 @@ enum { kOpInit = 0, kOpRescale = 1, kOpStep = 2 };
 // Host-side compiled network.
 struct HostNet {
   int S = 0, R = 0, nnzJ = 0, nnzLU = 0, nseg = 0, kdense = 0;
+  int head_ints = 0;  // 2 (kdense + 1) + entries of the sparse pivots' lists
   double lu_flops = 0;
   std::vector<int> perm, iperm, rprod;
   std::vector<int> rtype, ra, rb;
@@ -94,6 +95,7 @@ struct SolveArgs {
   double* ws;      // per-CTA workspace, ws_stride doubles per CTA
   long long ws_stride;
   int* counter;    // next-cell counter, zero before the launch
+  int piv_ints;    // pivot-list ints staged in shared memory (set by launch_solver)
 };
 
 struct GradArgs {
@@ -126,10 +128,11 @@ struct SolverPlan {
   size_t smem = 0;          // dynamic shared memory per CTA
   long long ws_stride = 0;  // per-CTA global workspace, in doubles
   int occupancy = 0;        // CTAs per SM (0: cannot launch)
+  int piv_ints = 0;         // staged pivot-list ints in shared memory (0: none)
 };
-size_t smem_bytes(int S, int R, int nseg, bool mixed, bool gm);
+size_t smem_bytes(int S, int R, int nseg, bool mixed, bool gm, int piv_ints = 0);
 long long workspace_doubles(int S, int R, int nnzJ, bool mixed, bool gm);
-SolverPlan plan_solver(int S, int R, int nseg, int nnzJ, bool mixed);
+SolverPlan plan_solver(int S, int R, int nseg, int nnzJ, bool mixed, int head_ints);
 // Launch the solver; returns a cudaError_t value.
 int launch_solver(const SolveArgs& a, const SolverPlan& p, int grid, void* stream);
 int device_sm_count();

@@ -234,13 +234,34 @@ std::string compile_network(const cbx_species* sp, int S, const cbx_reaction* rx
   }
   n.nnzLU = 0;
   for (uint8_t v : F) n.nnzLU += v;
-  // first pivot from which every L column and U row is the full range k+1..S-1
-  n.kdense = S;
-  for (int k = S - 1; k >= 0; --k) {
-    const int nl = n.piv_lptr[k + 1] - n.piv_lptr[k], nu = n.piv_uptr[k + 1] - n.piv_uptr[k];
-    if (nl != S - k - 1 || nu != S - k - 1) break;
-    n.kdense = k;
+  // Pivots k >= kdense are factored as if L(:,k) and U(k,:) were the full
+  // ranges k+1..S-1: an entry outside the pattern holds an exact zero, so the
+  // extra a_ik u_kj terms are exact zeros and the result is unchanged; in
+  // exchange the kernel needs no index lists there. kdense minimises a cost
+  // model of the FP64 kernel per pivot: each warp instruction covers 32
+  // columns of one row and takes ~20 SM cycles of the FP64 pipe, plus a fixed
+  // cost per pivot that is larger with index lists (their loads sit on the
+  // critical path) than with index ranges.
+  auto pivot_cost = [&](int k, bool dense) {
+    const int nl = dense ? S - k - 1 : n.piv_lptr[k + 1] - n.piv_lptr[k];
+    const int nu = dense ? S - k - 1 : n.piv_uptr[k + 1] - n.piv_uptr[k];
+    return 20.0 * nl * ((nu + 31) / 32) + (dense ? 900.0 : 2500.0);
+  };
+  {
+    double tail = 0.0, best = 0.0;
+    for (int k = 0; k < S; ++k) best += pivot_cost(k, false);
+    n.kdense = S;
+    double head = best;
+    for (int k = S - 1; k >= 0; --k) {
+      head -= pivot_cost(k, false);
+      tail += pivot_cost(k, true);
+      if (head + tail < best) {
+        best = head + tail;
+        n.kdense = k;
+      }
+    }
   }
+  n.head_ints = 2 * (n.kdense + 1) + n.piv_lptr[n.kdense] + n.piv_uptr[n.kdense];
   n.lu_flops = flops;
   return "";
 }

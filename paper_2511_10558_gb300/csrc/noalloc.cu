@@ -76,7 +76,7 @@ extern "C" int cbx_solve_noalloc(cbx_network* net, const cbx_cell_params* phi, c
   }
   const HostNet& h = net->host;
   const bool mixed = o.precision == CBX_MIXED;
-  const SolverPlan plan = plan_solver(h.S, h.R, h.nseg, h.nnzJ, mixed);
+  const SolverPlan plan = plan_solver(h.S, h.R, h.nseg, h.nnzJ, mixed, h.head_ints);
   const int occ = plan.occupancy;
   if (occ < 1) return fail(CBX_E_TOO_LARGE, "network too large for the solver");
   const long long stride = plan.ws_stride;

@@ -79,7 +79,7 @@ namespace {
 // Device bytes a request needs: inputs, outputs, status, workspace.
 size_t request_bytes(cbx_network* net, int C, bool mixed) {
   const HostNet& h = net->host;
-  const SolverPlan p = plan_solver(h.S, h.R, h.nseg, h.nnzJ, mixed);
+  const SolverPlan p = plan_solver(h.S, h.R, h.nseg, h.nnzJ, mixed, h.head_ints);
   const int grid = std::max(1, std::min(C, std::max(1, p.occupancy) * device_sm_count()));
   return (size_t)C * (sizeof(cbx_cell_params) + 2 * h.S * sizeof(double) + sizeof(int)) +
          (size_t)grid * p.ws_stride * sizeof(double) + 4096;

@@ -227,23 +227,38 @@ __device__ void build_matrix(const DevNet& n, const double* Jv, double c, LT* M)
 // rank-1 update a_ij -= a_ik u_kj (rows i of L(:,k), columns j of U(k,:)) with
 // no separate scaling phase: one barrier per pivot. Warp 0 updates row k+1
 // first and then prepares pivot k+1 (reciprocal pivot, row scaling) while the
-// other warps work on their rows. Pivots k >= kd have a fully dense trailing
-// block and use index ranges instead of the per-pivot lists.
+// other warps work on their rows. Pivots k >= kd are factored over the full
+// ranges k+1..S-1 (entries outside the pattern are exact zeros), without the
+// per-pivot index lists.
 
-__device__ __forceinline__ int lrow(const DevNet& n, bool dense, int k, int e) {
-  return dense ? k + 1 + e : __ldg(n.piv_l + e);
+// Index lists of the sparse pivots k < kd (from the network tables, or a
+// copy of their head in shared memory).
+struct PivLists {
+  int S, kd;
+  const int* lptr;  // [kd+1]
+  const int* l;
+  const int* uptr;  // [kd+1]
+  const int* u;
+};
+
+__device__ __forceinline__ PivLists global_pivots(const DevNet& n) {
+  return PivLists{n.S, n.kdense, n.piv_lptr, n.piv_l, n.piv_uptr, n.piv_u};
+}
+
+__device__ __forceinline__ int lrow(const PivLists& P, bool dense, int k, int e) {
+  return dense ? k + 1 + e : P.l[e];
 }
 
 // Reciprocal pivot and scaling of row k of U (warp-wide call).
-__device__ void prep_pivot(const DevNet& n, double* M, double* invd, int k, int kd, int lane) {
-  const int S = n.S, ld = lead_dim(S);
+__device__ void prep_pivot(const PivLists& P, double* M, double* invd, int k, int lane) {
+  const int S = P.S, ld = lead_dim(S), kd = P.kd;
   const double inv = __drcp_rn(M[k * ld + k]);  // correctly rounded: equals 1.0 / pivot
   if (lane == 0) invd[k] = inv;
   if (k >= kd) {
     for (int j = k + 1 + lane; j < S; j += 32) M[k * ld + j] *= inv;
   } else {
-    const int u1 = __ldg(n.piv_uptr + k + 1);
-    for (int e = __ldg(n.piv_uptr + k) + lane; e < u1; e += 32) M[k * ld + __ldg(n.piv_u + e)] *= inv;
+    const int u1 = P.uptr[k + 1];
+    for (int e = P.uptr[k] + lane; e < u1; e += 32) M[k * ld + P.u[e]] *= inv;
   }
 }
 
@@ -280,9 +295,9 @@ __device__ __forceinline__ void update_rows(double* r0, double* r1, bool two, in
 // (in the dense trailing block the scaling by 1/pivot is applied in registers
 // before the single store); the other warps take the other rows in pairs.
 template <int MC>
-__device__ __forceinline__ void crout_rows(const DevNet& n, double* M, double* invd, int k, int kd, bool dense,
+__device__ __forceinline__ void crout_rows(const PivLists& P, double* M, double* invd, int k, bool dense,
                                            int l0, int l1, int u0, int nu, bool next_in_l) {
-  const int ld = lead_dim(n.S);
+  const int ld = lead_dim(P.S);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int jc[MC];
   double uv[MC];
@@ -292,7 +307,7 @@ __device__ __forceinline__ void crout_rows(const DevNet& n, double* M, double* i
     jc[m] = 0;
     uv[m] = 0.0;
     if (b < nu) {
-      jc[m] = dense ? k + 1 + b : __ldg(n.piv_u + u0 + b);
+      jc[m] = dense ? k + 1 + b : P.u[u0 + b];
       uv[m] = M[k * ld + jc[m]];
     }
   }
@@ -314,7 +329,7 @@ __device__ __forceinline__ void crout_rows(const DevNet& n, double* M, double* i
       for (int m = 0; m < MC; ++m)
         if (lane + 32 * m < nu) r0[jc[m]] = x0[m];
       __syncwarp();
-      prep_pivot(n, M, invd, k + 1, kd, lane);
+      prep_pivot(P, M, invd, k + 1, lane);
     }
     return;
   }
@@ -323,16 +338,16 @@ __device__ __forceinline__ void crout_rows(const DevNet& n, double* M, double* i
   const int wi = next_in_l ? w - 1 : w;
   for (int e = first + wi; e < l1; e += 2 * nw) {
     const bool two = e + nw < l1;
-    double* r0 = M + lrow(n, dense, k, e) * ld;
-    double* r1 = two ? M + lrow(n, dense, k, e + nw) * ld : r0;
+    double* r0 = M + lrow(P, dense, k, e) * ld;
+    double* r1 = two ? M + lrow(P, dense, k, e + nw) * ld : r0;
     update_rows<MC>(r0, r1, two, k, jc, uv, nu, lane);
   }
 }
 
-__device__ void lu_crout64(const DevNet& n, double* M, double* invd) {
-  const int S = n.S, ld = lead_dim(S), kd = n.kdense;
+__device__ void lu_crout64(const PivLists& P, double* M, double* invd) {
+  const int S = P.S, ld = lead_dim(S), kd = P.kd;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (w == 0) prep_pivot(n, M, invd, 0, kd, lane);
+  if (w == 0) prep_pivot(P, M, invd, 0, lane);
   __syncthreads();
   for (int k = 0; k + 1 < S; ++k) {
     const bool dense = k >= kd;
@@ -343,26 +358,26 @@ __device__ void lu_crout64(const DevNet& n, double* M, double* invd) {
       u0 = 0;
       nu = S - k - 1;
     } else {
-      l0 = __ldg(n.piv_lptr + k);
-      l1 = __ldg(n.piv_lptr + k + 1);
-      u0 = __ldg(n.piv_uptr + k);
-      nu = __ldg(n.piv_uptr + k + 1) - u0;
+      l0 = P.lptr[k];
+      l1 = P.lptr[k + 1];
+      u0 = P.uptr[k];
+      nu = P.uptr[k + 1] - u0;
     }
-    const bool next_in_l = l1 > l0 && lrow(n, dense, k, l0) == k + 1;
-    if (w == 0 && !next_in_l) prep_pivot(n, M, invd, k + 1, kd, lane);
+    const bool next_in_l = l1 > l0 && lrow(P, dense, k, l0) == k + 1;
+    if (w == 0 && !next_in_l) prep_pivot(P, M, invd, k + 1, lane);
     if (nu > 0) {
       switch ((nu + 31) >> 5) {
-        case 1: crout_rows<1>(n, M, invd, k, kd, dense, l0, l1, u0, nu, next_in_l); break;
-        case 2: crout_rows<2>(n, M, invd, k, kd, dense, l0, l1, u0, nu, next_in_l); break;
-        case 3: crout_rows<3>(n, M, invd, k, kd, dense, l0, l1, u0, nu, next_in_l); break;
-        case 4: crout_rows<4>(n, M, invd, k, kd, dense, l0, l1, u0, nu, next_in_l); break;
-        case 5: crout_rows<5>(n, M, invd, k, kd, dense, l0, l1, u0, nu, next_in_l); break;
-        case 6: crout_rows<6>(n, M, invd, k, kd, dense, l0, l1, u0, nu, next_in_l); break;
-        case 7: crout_rows<7>(n, M, invd, k, kd, dense, l0, l1, u0, nu, next_in_l); break;
-        default: crout_rows<8>(n, M, invd, k, kd, dense, l0, l1, u0, nu, next_in_l); break;
+        case 1: crout_rows<1>(P, M, invd, k, dense, l0, l1, u0, nu, next_in_l); break;
+        case 2: crout_rows<2>(P, M, invd, k, dense, l0, l1, u0, nu, next_in_l); break;
+        case 3: crout_rows<3>(P, M, invd, k, dense, l0, l1, u0, nu, next_in_l); break;
+        case 4: crout_rows<4>(P, M, invd, k, dense, l0, l1, u0, nu, next_in_l); break;
+        case 5: crout_rows<5>(P, M, invd, k, dense, l0, l1, u0, nu, next_in_l); break;
+        case 6: crout_rows<6>(P, M, invd, k, dense, l0, l1, u0, nu, next_in_l); break;
+        case 7: crout_rows<7>(P, M, invd, k, dense, l0, l1, u0, nu, next_in_l); break;
+        default: crout_rows<8>(P, M, invd, k, dense, l0, l1, u0, nu, next_in_l); break;
       }
     } else if (w == 0 && next_in_l) {
-      prep_pivot(n, M, invd, k + 1, kd, lane);
+      prep_pivot(P, M, invd, k + 1, lane);
     }
     __syncthreads();
   }
@@ -794,11 +809,14 @@ struct Smem {
   void* invd;
   double *D, *y, *yp, *dv, *f, *wsc, *psi, *dy, *w, *tmp, *r, *part, *red, *Tm;
   float* v32;
+  int* pstage;   // staged pivot lists (FP64 shared-memory solver), or none
+  PivLists piv;  // the lists the LU reads
 };
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
-__host__ __device__ inline size_t layout(int S, int R, int nseg, bool mixed, bool gm, unsigned char* base, Smem* s) {
+__host__ __device__ inline size_t layout(int S, int R, int nseg, bool mixed, bool gm, unsigned char* base, Smem* s,
+                                         int piv_ints = 0) {
   const size_t lt = mixed ? sizeof(float) : sizeof(double);
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -824,12 +842,33 @@ __host__ __device__ inline size_t layout(int S, int R, int nseg, bool mixed, boo
   t.red = (double*)take(64 * 8);
   t.Tm = (double*)take(kMaxOrder * kMaxOrder * 8);
   t.v32 = (float*)take(mixed ? S * 4 : 0);
+  t.pstage = (int*)take((size_t)piv_ints * 4);
   if (s) *s = t;
   return off;
 }
 
-size_t smem_bytes(int S, int R, int nseg, bool mixed, bool gm) {
-  return layout(S, R, nseg, mixed, gm, nullptr, nullptr);
+size_t smem_bytes(int S, int R, int nseg, bool mixed, bool gm, int piv_ints) {
+  return layout(S, R, nseg, mixed, gm, nullptr, nullptr, piv_ints);
+}
+
+// Copy the index lists of the sparse pivots (k < kd: pointers and entries)
+// into shared memory once per CTA, so that the LU's per-pivot index loads
+// are shared-memory loads rather than L2 round trips on its critical path.
+__device__ void stage_pivots(const DevNet& n, Smem& s) {
+  const int kd = n.kdense;
+  const int nl = n.piv_lptr[kd], nu = n.piv_uptr[kd];
+  int* lp = s.pstage;
+  int* up = lp + (kd + 1);
+  int* l = up + (kd + 1);
+  int* u = l + nl;
+  for (int i = threadIdx.x; i <= kd; i += NT) {
+    lp[i] = n.piv_lptr[i];
+    up[i] = n.piv_uptr[i];
+  }
+  for (int i = threadIdx.x; i < nl; i += NT) l[i] = n.piv_l[i];
+  for (int i = threadIdx.x; i < nu; i += NT) u[i] = n.piv_u[i];
+  __syncthreads();
+  s.piv = PivLists{n.S, kd, lp, l, up, u};
 }
 
 long long workspace_doubles(int S, int R, int nnzJ, bool mixed, bool gm) {
@@ -962,7 +1001,7 @@ __device__ void factor(Cell<LT, GM>& c, double cc) {
     if constexpr (sizeof(LT) == 4)
       lu_blocked<LT, false>(c.M, (LT*)c.s.invd, c.n.S, lead_dim(c.n.S));
     else
-      lu_crout64(c.n, c.M, (double*)c.s.invd);
+      lu_crout64(c.s.piv, c.M, (double*)c.s.invd);
   }
   if (threadIdx.x == 0) c.st->lu_factors++;
 }
@@ -1222,7 +1261,11 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(const SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_cell;
   Smem s;
-  layout(a.net.S, a.net.R, a.net.nseg, sizeof(LT) == 4, GM, smem_raw, &s);
+  layout(a.net.S, a.net.R, a.net.nseg, sizeof(LT) == 4, GM, smem_raw, &s, a.piv_ints);
+  s.piv = global_pivots(a.net);
+  if constexpr (!GM && sizeof(LT) == 8) {
+    if (a.piv_ints > 0) stage_pivots(a.net, s);
+  }
   double* ws = a.ws + (size_t)blockIdx.x * a.ws_stride;
   for (;;) {
     if (threadIdx.x == 0) s_cell = atomicAdd(a.counter, 1);
@@ -1250,13 +1293,18 @@ static int occupancy_t(size_t sm) {
   return e == cudaSuccess ? blocks : 0;
 }
 
-SolverPlan plan_solver(int S, int R, int nseg, int nnzJ, bool mixed) {
+SolverPlan plan_solver(int S, int R, int nseg, int nnzJ, bool mixed, int head_ints) {
   SolverPlan p;
   p.mixed = mixed;
   const size_t optin = device_smem_optin();
   // shared-memory matrix when it fits and the FP64 LU's register tiling allows (S <= 256)
   p.gm = !(S <= 32 * kMaxColRegs && smem_bytes(S, R, nseg, mixed, false) <= optin);
   p.smem = smem_bytes(S, R, nseg, mixed, p.gm);
+  // FP64 shared-memory solver: stage the sparse pivots' lists when they fit
+  if (!mixed && !p.gm && smem_bytes(S, R, nseg, false, false, head_ints) <= optin) {
+    p.piv_ints = head_ints;
+    p.smem = smem_bytes(S, R, nseg, false, false, head_ints);
+  }
   p.ws_stride = workspace_doubles(S, R, nnzJ, mixed, p.gm);
   p.occupancy = 0;
   if (S > 2 * NT || p.smem > optin) return p;
@@ -1267,8 +1315,10 @@ SolverPlan plan_solver(int S, int R, int nseg, int nnzJ, bool mixed) {
   return p;
 }
 
-int launch_solver(const SolveArgs& a, const SolverPlan& p, int grid, void* stream) {
+int launch_solver(const SolveArgs& a0, const SolverPlan& p, int grid, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
+  SolveArgs a = a0;
+  a.piv_ints = p.piv_ints;
   if (p.mixed) return p.gm ? launch_t<float, true>(a, p.smem, grid, st) : launch_t<float, false>(a, p.smem, grid, st);
   return p.gm ? launch_t<double, true>(a, p.smem, grid, st) : launch_t<double, false>(a, p.smem, grid, st);
 }
@@ -1461,7 +1511,7 @@ __global__ void __launch_bounds__(NT, 1) grad_kernel(const GradArgs a) {
           const double c = v / a.gam[q];
           jacobian(n, kap, s.y, g, Jv);
           build_matrix<double>(n, Jv, c, M);
-          lu_crout64(n, M, invd);
+          lu_crout64(global_pivots(n), M, invd);
           forwardT_crout64(M, S, s.dy);
           for (int i = threadIdx.x; i < S; i += NT) s.dy[i] *= invd[i];
           __syncthreads();
