@@ -118,38 +118,56 @@ __device__ void rate_coefficients(const DevNet& n, const cbx_cell_params& p, dou
 }
 
 // f = nu r(y): reaction rates into r, signed segment sums into part, then
-// per-species sums of the segments (fixed order: bitwise reproducible).
+// per-species sums of the segments (fixed order: bitwise reproducible). The
+// network tables stream from L2, so each thread issues all its table loads
+// of a pass before it uses any of them (one round trip instead of one per
+// entry).
+constexpr int kRatesPerPass = 8;
 __device__ void rhs(const DevNet& n, const double* __restrict__ kap, const double* y, double* f,
                     double* r, double* part) {
-  for (int j = threadIdx.x; j < n.R; j += NT) {
-    const int b = __ldg(n.rb + j);
-    double v = kap[j] * y[__ldg(n.ra + j)];
-    if (b >= 0) v *= y[b];
-    r[j] = v;
+  for (int j0 = threadIdx.x; j0 < n.R; j0 += kRatesPerPass * NT) {
+    int ia[kRatesPerPass], ib[kRatesPerPass];
+    double kv[kRatesPerPass];
+#pragma unroll
+    for (int u = 0; u < kRatesPerPass; ++u) {
+      const int j = j0 + u * NT;
+      const bool ok = j < n.R;
+      ia[u] = ok ? __ldg(n.ra + j) : 0;
+      ib[u] = ok ? __ldg(n.rb + j) : -1;
+      kv[u] = ok ? kap[j] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kRatesPerPass; ++u) {
+      const int j = j0 + u * NT;
+      if (j < n.R) {
+        double v = kv[u] * y[ia[u]];
+        if (ib[u] >= 0) v *= y[ib[u]];
+        r[j] = v;
+      }
+    }
   }
   __syncthreads();
-  for (int s = threadIdx.x; s < n.nseg; s += NT) {
+  for (int sg = threadIdx.x; sg < n.nseg; sg += NT) {
+    const int e0 = __ldg(n.seg_ptr + sg), len = __ldg(n.seg_ptr + sg + 1) - e0;
+    int t[kSegLen];
+#pragma unroll
+    for (int u = 0; u < kSegLen; ++u) t[u] = u < len ? __ldg(n.rhs_ent + e0 + u) : 0;
+    double v[kSegLen];
+#pragma unroll
+    for (int u = 0; u < kSegLen; ++u) v[u] = r[t[u] >> 1];
     double acc0 = 0.0, acc1 = 0.0;
-    const int e1 = __ldg(n.seg_ptr + s + 1);
-    int e = __ldg(n.seg_ptr + s);
-    for (; e + 2 <= e1; e += 2) {
-      const int t0 = __ldg(n.rhs_ent + e), t1 = __ldg(n.rhs_ent + e + 1);
-      const double v0 = r[t0 >> 1], v1 = r[t1 >> 1];
-      acc0 += (t0 & 1) ? -v0 : v0;
-      acc1 += (t1 & 1) ? -v1 : v1;
+#pragma unroll
+    for (int u = 0; u < kSegLen; u += 2) {
+      if (u < len) acc0 += (t[u] & 1) ? -v[u] : v[u];
+      if (u + 1 < len) acc1 += (t[u + 1] & 1) ? -v[u + 1] : v[u + 1];
     }
-    if (e < e1) {
-      const int t0 = __ldg(n.rhs_ent + e);
-      const double v0 = r[t0 >> 1];
-      acc0 += (t0 & 1) ? -v0 : v0;
-    }
-    part[s] = acc0 + acc1;
+    part[sg] = acc0 + acc1;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < n.S; i += NT) {
     double acc = 0.0;
     const int s1 = __ldg(n.spec_seg + i + 1);
-    for (int s = __ldg(n.spec_seg + i); s < s1; ++s) acc += part[s];
+    for (int sg = __ldg(n.spec_seg + i); sg < s1; ++sg) acc += part[sg];
     f[i] = acc;
   }
   __syncthreads();
