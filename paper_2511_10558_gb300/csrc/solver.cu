@@ -704,11 +704,37 @@ __device__ __forceinline__ void trailing_update(LT* M, int S, int ld, int kb, in
 }
 
 // U_bb^{-1} of every diagonal block, in place (strict upper part; the
-// diagonal reciprocals stay in invd): one warp per block, columns left to
-// right, X[0:j, j] = -X[0:j, 0:j] U[0:j, j] / U_jj with X[0:j, 0:j] (already
+// diagonal reciprocals stay in invd). FP32 form: one warp per block, lane j
+// solves U_bb x = e_j by back substitution in registers (the block's entries
+// are broadcast loads), and the warp overwrites the block once all its lanes
+// have read it.
+template <typename LT, bool FULL>
+__device__ __forceinline__ void invert_upper_block(LT* U, const LT* invd, int ld, int nb, int lane) {
+  LT x[NB];
+#pragma unroll
+  for (int r = NB - 1; r >= 0; --r) {
+    x[r] = LT(0);
+    if (FULL || r < nb) {
+      LT acc = r == lane ? LT(1) : LT(0);
+#pragma unroll
+      for (int c = r + 1; c < NB; ++c)
+        if (FULL || c < nb) acc -= U[r * ld + c] * x[c];
+      x[r] = acc * invd[r];
+    }
+  }
+  __syncwarp();
+  if (lane < nb) {
+#pragma unroll
+    for (int r = 0; r < NB - 1; ++r)
+      if (r < lane) U[r * ld + lane] = x[r];
+  }
+}
+
+// FP64 form (fewer registers than a column of NB doubles per lane): one warp
+// per block, columns left to right, X[0:j, j] = -X[0:j, 0:j] U[0:j, j] / U_jj with X[0:j, 0:j] (already
 // in place) and the still-original column j; lanes take the rows r < j.
 template <typename LT>
-__device__ void invert_upper_blocks(LT* M, const LT* invd, int S, int ld) {
+__device__ void invert_upper_blocks_cols(LT* M, const LT* invd, int S, int ld) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nblk = (S + NB - 1) / NB;
   for (int b = warp; b < nblk; b += NW) {
@@ -732,6 +758,22 @@ __device__ void invert_upper_blocks(LT* M, const LT* invd, int S, int ld) {
       if (lane < j) U[lane * ld + j] = -invd[kb + j] * acc;
       __syncwarp();
     }
+  }
+  __syncthreads();
+}
+
+template <typename LT>
+__device__ void invert_upper_blocks(LT* M, const LT* invd, int S, int ld) {
+  if constexpr (sizeof(LT) == 8) {
+    invert_upper_blocks_cols<LT>(M, invd, S, ld);
+    return;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nblk = (S + NB - 1) / NB;
+  for (int b = warp; b < nblk; b += NW) {
+    const int kb = b * NB, nb = min(NB, S - kb);
+    if (nb == NB) invert_upper_block<LT, true>(M + kb * ld + kb, invd + kb, ld, nb, lane);
+    else invert_upper_block<LT, false>(M + kb * ld + kb, invd + kb, ld, nb, lane);
   }
   __syncthreads();
 }
