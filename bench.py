@@ -153,38 +153,54 @@ _NET_CACHE = {}
 
 
 def _oracle_worker(args):
-    S, R, phis, x0 = args
+    S, R, idx, phis, x0 = args
     from oracle import bdf
     if (S, R) not in _NET_CACHE:
         _NET_CACHE[(S, R)] = synth.make_network(S, R)
     net = _NET_CACHE[(S, R)]
-    for phi in phis:
-        bdf.solve_cell(net, phi, x0, 0.0, T_END, RTOL, ATOL)
-    return len(phis)
+    return [(i, bdf.solve_cell(net, phi, x0, 0.0, T_END, RTOL, ATOL).x) for i, phi in zip(idx, phis)]
 
 
 def time_oracle(n_cells, cores):
-    """Oracle cell-solves/s on `cores` host processes over a seeded sample."""
+    """Oracle cell-solves/s on `cores` host processes over a seeded sample (the
+    first n_cells cells), with the sample's results [S, n_cells]."""
     net = synth.make_network(S_SP, R_RX)
     x0 = synth.initial_abundances(net)
     phis = synth.cells(CELLS)[:n_cells]
-    chunks = [(S_SP, R_RX, phis[i::cores], x0) for i in range(cores)]
+    idx = np.arange(n_cells)
+    chunks = [(S_SP, R_RX, idx[i::cores], phis[i::cores], x0) for i in range(cores)]
     ctx = mp.get_context("spawn")
     env_before = os.environ.get("OPENBLAS_NUM_THREADS")
     os.environ["OPENBLAS_NUM_THREADS"] = "1"
     os.environ["OMP_NUM_THREADS"] = "1"
     try:
         with ctx.Pool(cores) as pool:
-            pool.map(_oracle_worker, [(S_SP, R_RX, phis[:1], x0)] * cores)  # import + warm
+            pool.map(_oracle_worker, [(S_SP, R_RX, idx[:1], phis[:1], x0)] * cores)  # import + warm
             t = time.perf_counter()
-            done = sum(pool.map(_oracle_worker, chunks))
+            parts = pool.map(_oracle_worker, chunks)
             dt = time.perf_counter() - t
     finally:
         if env_before is None:
             os.environ.pop("OPENBLAS_NUM_THREADS", None)
         else:
             os.environ["OPENBLAS_NUM_THREADS"] = env_before
-    return done / dt, dt
+    xs = np.empty((S_SP, n_cells))
+    for part in parts:
+        for i, x in part:
+            xs[:, i] = x
+    return n_cells / dt, dt, xs
+
+
+def parity_summary(x_gpu, x_ref, tol=1e-4, floor=1e-12):
+    """Per sampled cell, the largest relative difference over species above
+    `floor`; how many cells are within `tol`."""
+    rel = []
+    for c in range(x_ref.shape[1]):
+        big = x_ref[:, c] > floor
+        rel.append(float(np.max(np.abs(x_gpu[big, c] / x_ref[big, c] - 1))) if big.any() else 0.0)
+    rel = np.array(rel)
+    return {"cells": int(rel.size), "tol": tol, "within_tol": int((rel <= tol).sum()),
+            "max_rel": float(rel.max()), "median_rel": float(np.median(rel))}
 
 
 def run_reference(args):
@@ -197,7 +213,7 @@ def run_reference(args):
     for _ in range(args.warmup if args.warmup < 1 else 1):
         time_oracle(cores, cores)
     for _ in range(args.steps):
-        v, _ = time_oracle(n, cores)
+        v, _, _ = time_oracle(n, cores)
         vals.append(v)
     v = float(np.mean(vals))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "cell-solves/s", "n_gpus": ws,
@@ -276,6 +292,7 @@ def run_gpu(args):
         ms64 = timed(carbox.CBX_FP64, args.steps, args.warmup) if args.only != "mixed" else [float("nan")]
     st64 = carbox.stats_dict(stats.cpu().numpy())
     ok64 = int((status == 0).sum().item())
+    x64_sample = x_out[:, :max(args.ref_cells, os.cpu_count() or 1)].cpu().numpy()
     t_max = max_over_ranks(sum(ms64) / 1e3, dev)
     value = weak_value(ws, CELLS, args.steps, t_max)
     ms_per_step = 1e3 * t_max / args.steps
@@ -295,6 +312,7 @@ def run_gpu(args):
         return
     stmx = carbox.stats_dict(stats.cpu().numpy())
     okmx = int((status == 0).sum().item())
+    xmx_sample = x_out[:, :max(args.ref_cells, os.cpu_count() or 1)].cpu().numpy()
     mixed_value = CELLS * len(msmx) / (sum(msmx) / 1e3)
     latmx = (stmx["t_end_ns"] - stmx["t_begin_ns"]) / 1e6
 
@@ -316,13 +334,15 @@ def run_gpu(args):
 
     if rank != 0:
         return
-    cpu = None
+    cpu = parity = None
     if ws == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         ncell = max(cores, args.ref_cells)
-        v, dt = time_oracle(ncell, cores)
+        v, dt, x_ref = time_oracle(ncell, cores)
         cpu = {"value": v, "unit": "cell-solves/s", "cores": cores, "kind": "oracle",
                "sample": f"first {ncell} of the {CELLS} seeded cells, spawn pool of {cores} processes, {dt:.1f} s"}
+        parity = {"fp64": parity_summary(x64_sample[:, :ncell], x_ref),
+                  "mixed": parity_summary(xmx_sample[:, :ncell], x_ref)}
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     traffic = None
     if os.path.exists(prof):
@@ -352,6 +372,7 @@ def run_gpu(args):
                      "kernel": "solve_kernel<double> (FP64 pipe)",
                      "flops_per_launch": fp64_flops, "flop_split": {k: v for k, v in fl.items()}},
         "cpu_baseline": cpu,
+        "parity_sample": parity,
         "e2e": {"value": e2e_value, "unit": "cell-solves/s",
                 "h2d_bytes_per_step": int(phi_h.nbytes + x0_h.nbytes),
                 "d2h_bytes_per_step": int(x0_h.nbytes + CELLS * 4)},

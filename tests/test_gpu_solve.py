@@ -163,3 +163,35 @@ def test_large_500_global_matrix(dev, net500, prec):
     for c in [0, C - 1]:
         ref = bdf.solve_cell(net500, phi[c], x0[:, c], 0.0, t_end, 1e-4, 1e-20)
         assert_twin(x[:, c], ref.x, f"500-species cell {c}")
+
+
+def test_parity_where_step_programs_differ(dev, net150):
+    # Rounding differences between the CUDA path and the oracle can flip an
+    # accept/reject or order decision of the step controller; the two then
+    # follow different, equally valid step programs and differ by the method's
+    # global error (up to a few 1e-3 at rtol 1e-4), not by rounding. Cells 3
+    # and 9 of this sample did so when this test was written. A cell is
+    # accepted when it is within 1e-4 of the oracle, or when, against a
+    # reference at rtol 1e-8, its error is at most twice the larger of the
+    # oracle's own error and 1e-3.
+    cells = [3, 9, 21, 46]
+    phi = synth.cells(1216)[cells]
+    x0 = np.repeat(synth.initial_abundances(net150)[:, None], len(cells), axis=1)
+    t_end = 1e6 * YR
+    N = carbox.Network.from_synth(net150)
+    x, st, _ = gpu_solve(N, phi, x0, t_end, dev)
+    assert np.all(st == carbox.CBX_CELL_OK)
+    flipped = 0
+    for j in range(len(cells)):
+        ref = bdf.solve_cell(net150, phi[j], x0[:, j], 0.0, t_end, 1e-4, 1e-20).x
+        big = ref > FLOOR
+        if np.max(np.abs(x[big, j] / ref[big] - 1)) <= TOL:
+            continue
+        flipped += 1
+        tight = bdf.solve_cell(net150, phi[j], x0[:, j], 0.0, t_end, 1e-8, 1e-26).x
+        big = tight > FLOOR
+        e_gpu = np.max(np.abs(x[big, j] / tight[big] - 1))
+        e_orc = np.max(np.abs(ref[big] / tight[big] - 1))
+        print(f"cell {cells[j]}: error vs rtol-1e-8 reference gpu {e_gpu:.2e}, oracle {e_orc:.2e}")
+        assert e_gpu <= 2 * max(e_orc, 1e-3), (cells[j], e_gpu, e_orc)
+    print("cells on a different step program:", flipped)
