@@ -533,6 +533,82 @@ def run_adjoint(args):
     print(json.dumps(res), flush=True)
 
 
+def run_zeta(args):
+    """Cosmic-ray sweep with sensitivities (synthetic analog of the paper's zeta study,
+    Sec. 4 / Fig. 2): 150 sp, the reference cell (n_H 1e4, T 20 K, A_V 5, G0 1) at C
+    values of zeta / zeta_0 log-spaced over [1e-2, 1e4], 0 -> 1e7 yr, FP64 forward with
+    recording, then the adjoint of L = log10 x_e(t_f) per cell: d log10 x_e / d ln zeta
+    (and d/d ln G0, d/dA_V, d/d ln n_H, d/dT) for every cell of the sweep."""
+    torch, dev, carbox = _gpu_setup()
+    from oracle import adjoint as adj
+    stream = torch.cuda.current_stream(dev)
+    net = synth.make_network(S_SP, R_RX)
+    N = carbox.Network.from_synth(net)
+    C = 1024
+    t_end = 1e7 * synth.YEAR
+    ratio = 10.0 ** np.linspace(-2.0, 4.0, C)
+    phi_h = np.repeat(synth.one_cell(), C, axis=0)
+    phi_h[:, 4] = synth.ZETA0 * ratio
+    x0_h = np.repeat(synth.initial_abundances(net)[:, None], C, axis=1)
+    phi = torch.tensor(phi_h, device=dev).contiguous()
+    x0 = torch.tensor(x0_h, device=dev).contiguous()
+    tape = carbox.Tape(N, C, 3000)
+    o = carbox.options(rtol=RTOL, atol=ATOL, precision=carbox.CBX_FP64)
+    carbox.solve_record(N, tape, phi, x0, 0.0, t_end, o)   # warm-up
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record(stream)
+    x, st = carbox.solve_record(N, tape, phi, x0, 0.0, t_end, o)
+    e[1].record(stream)
+    torch.cuda.synchronize()
+    xh = x.cpu().numpy()
+    ie = net.index("e-")
+    cot = np.zeros_like(xh)
+    cot[ie, :] = 1.0 / (xh[ie, :] * np.log(10.0))   # L = log10 x_e
+    cot_d = torch.tensor(cot, device=dev).contiguous()
+    carbox.grad_env(tape, cot_d, C)  # warm-up
+    torch.cuda.synchronize()
+    e[2].record(stream)
+    ga, gn, gt, gz, gg, gav = carbox.grad_env(tape, cot_d, C)
+    e[3].record(stream)
+    torch.cuda.synchronize()
+    fwd_ms, bwd_ms = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
+    gz_h = gz.cpu().numpy()
+    # checks where the sensitivity is not saturated (|g| >= 0.1 of its largest
+    # value; at high zeta this synthetic network is fully ionised and the
+    # derivative is zero to rounding, where relative errors mean nothing)
+    live = np.flatnonzero(np.abs(gz_h) >= 0.1 * np.abs(gz_h).max())
+    checks = []
+    for c in sorted({int(live[0]), int(np.argmax(np.abs(gz_h))), int(live[-1])}):
+        prog = []
+        for kind, q, v in tape.program(c):
+            prog.append(("init", v) if kind == 0 else ("rescale", q, v) if kind == 1 else ("step", q, v, 0.0, None))
+        xr, prog_r = adj.replay(net, phi_h[c], x0_h[:, c], prog)
+        cr = np.zeros(S_SP)
+        cr[ie] = 1.0 / (xr[ie] * np.log(10.0))
+        g = adj.adjoint(net, phi_h[c], x0_h[:, c], prog_r, cr)
+        z_ref = adj.environment_gradients(net, g[0])[0]
+        eps = 1e-6
+        pp, pm = phi_h[c].copy(), phi_h[c].copy()
+        pp[4] *= np.exp(eps)
+        pm[4] *= np.exp(-eps)
+        fd = (np.log10(adj.replay(net, pp, x0_h[:, c], prog)[0][ie]) -
+              np.log10(adj.replay(net, pm, x0_h[:, c], prog)[0][ie])) / (2 * eps)
+        checks.append({"cell": c, "zeta_over_zeta0": float(ratio[c]), "dlog10xe_dlnzeta": float(gz_h[c]),
+                       "rel_err_vs_oracle_adjoint": abs(gz_h[c] / z_ref - 1), "rel_err_vs_fd": abs(gz_h[c] / fd - 1)})
+    ok = st.cpu().numpy() == 0
+    grid = [0, C // 4, C // 2, 3 * C // 4, C - 1]
+    res = {"config": "zeta", "workload": f"{S_SP} species / {R_RX} reactions, {C} cells, zeta/zeta0 log-spaced in "
+                                          "[1e-2, 1e4], reference cell otherwise, 0 -> 1e7 yr, FP64; L = log10 x_e",
+           "forward_record_ms": fwd_ms, "adjoint_ms": bwd_ms, "cells_ok": int(ok.sum()),
+           "cell_solves_per_s_with_gradients": C / ((fwd_ms + bwd_ms) / 1e3),
+           "x_e": {f"{ratio[c]:.3g}": float(xh[ie, c]) for c in grid},
+           "sensitive_range_zeta_over_zeta0": [float(ratio[live[0]]), float(ratio[live[-1]])],
+           "dlog10xe_dlnzeta": {f"{ratio[c]:.3g}": float(gz_h[c]) for c in grid},
+           "checks": checks}
+    print(json.dumps(res), flush=True)
+
+
 def run_serving(args):
     """Config 5: Poisson requests over 32/150/500-species networks through cbx_server."""
     torch, dev, carbox = _gpu_setup()
@@ -604,7 +680,7 @@ def main():
     ap.add_argument("--only", choices=["fp64", "mixed"], default=None)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-large", action="store_true")
-    ap.add_argument("--config", choices=["bench", "large", "adjoint", "serving"], default="bench")
+    ap.add_argument("--config", choices=["bench", "large", "adjoint", "serving", "zeta"], default="bench")
     ap.add_argument("--duration", type=float, default=2.0, help="serving: seconds of Poisson arrivals")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean requests per second")
     args = ap.parse_args()
@@ -616,6 +692,8 @@ def main():
         run_adjoint(args)
     elif args.config == "serving":
         run_serving(args)
+    elif args.config == "zeta":
+        run_zeta(args)
     else:
         run_gpu(args)
 

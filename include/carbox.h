@@ -240,6 +240,20 @@ int cbx_grad(cbx_tape* tape, const double* cot_x, void* stream, double* g_logalp
              double* g_T);
 
 /*
+ * cbx_grad plus the gradients with respect to each cell's radiation and
+ * cosmic-ray environment (Sec. 3 asks for sensitivities to physical inputs):
+ *   g_lnzeta [C]  dL/d ln zeta: cosmic-ray coefficients are alpha_j zeta (Sec. 2),
+ *   g_lnG0   [C]  dL/d ln G0:   photo coefficients are alpha_j G0 exp(-gamma_j A_V)
+ *                               (App. B.1),
+ *   g_AV     [C]  dL/dA_V (mag), from the same photo form.
+ * Each is a fixed-order sum over the cell's per-reaction gradients
+ * dL/d ln k_j of the discrete adjoint (device pointers, any may be NULL).
+ * Other arguments, ownership and errors as for cbx_grad.
+ */
+int cbx_grad_env(cbx_tape* tape, const double* cot_x, void* stream, double* g_logalpha, double* g_lognH,
+                 double* g_T, double* g_lnzeta, double* g_lnG0, double* g_AV);
+
+/*
  * Read the recorded program of one cell to the host (for checks): kinds
  * (0 init, 1 rescale, 2 step), orders q and values (h0, rho or h); at most cap
  * entries. Returns the number of ops (>= 0) or a negative error code.

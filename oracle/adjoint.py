@@ -80,6 +80,19 @@ def adjoint(net, phi, x0, program, cot_x):
     return g_la, g_nH, g_T
 
 
+def environment_gradients(net, g_lnk):
+    """(dL/d ln zeta, dL/d ln G0, dL/dA_V) of one cell from its per-reaction
+    gradients dL/d ln k_j, which equal dL/d ln alpha_j because k_j is
+    proportional to alpha_j. Cosmic-ray coefficients are alpha_j zeta (Sec. 2);
+    photo coefficients alpha_j G0 exp(-gamma_j A_V) (App. B.1): so d ln k_j /
+    d ln zeta = 1 (cosmic ray), d ln k_j / d ln G0 = 1 and d ln k_j / dA_V =
+    -gamma_j (photo), and zero otherwise."""
+    g = np.asarray(g_lnk, dtype=float)
+    cr = net.rtype == chem.COSMIC_RAY
+    ph = net.rtype == chem.PHOTO
+    return float(g[cr].sum()), float(g[ph].sum()), float(-(net.gamma[ph] * g[ph]).sum())
+
+
 def replay(net, phi, x0, program, newton_tol=1e-13, max_iter=60):
     """Re-run a recorded program with each corrector solved to convergence.
 

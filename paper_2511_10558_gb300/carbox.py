@@ -97,6 +97,7 @@ def _load():
         "cbx_solve_record": (C.c_int, [P, P, P, C.c_int, C.c_double, C.c_double, C.POINTER(cbx_options), P, P, P,
                                        P, P]),
         "cbx_grad": (C.c_int, [P, P, P, P, P, P]),
+        "cbx_grad_env": (C.c_int, [P, P, P, P, P, P, P, P, P]),
         "cbx_tape_program": (C.c_int, [P, C.c_int, P, P, P, C.c_int]),
         "cbx_server_create": (C.c_int, [C.c_size_t, C.c_int, C.c_int, C.POINTER(P)]),
         "cbx_server_submit": (C.c_int, [P, P, P, P, C.c_int, C.c_double, C.c_double, C.POINTER(cbx_options),
@@ -298,6 +299,21 @@ def grad(tape, cot_x, n_cells, stream=None):
     check(lib.cbx_grad(tape.handle, _ptr(cot_x), C.c_void_p(stream.cuda_stream), _ptr(ga), _ptr(gn), _ptr(gt)),
           "cbx_grad")
     return ga, gn, gt
+
+
+def grad_env(tape, cot_x, n_cells, stream=None):
+    """cbx_grad_env: (dL/d ln alpha [R], dL/d ln n_H [C], dL/dT [C], dL/d ln zeta [C],
+    dL/d ln G0 [C], dL/dA_V [C]) for dL/dx(t_end) = cot_x [S, C]."""
+    import torch
+    assert cot_x.is_cuda and cot_x.dtype == torch.float64 and cot_x.is_contiguous()
+    dev = cot_x.device
+    ga = torch.empty(tape.net.R, dtype=torch.float64, device=dev)
+    out = [torch.empty(n_cells, dtype=torch.float64, device=dev) for _ in range(5)]
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    check(lib.cbx_grad_env(tape.handle, _ptr(cot_x), C.c_void_p(stream.cuda_stream), _ptr(ga),
+                           *[_ptr(t) for t in out]), "cbx_grad_env")
+    return (ga, *out)
 
 
 def _make_function():

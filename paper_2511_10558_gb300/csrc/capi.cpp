@@ -386,6 +386,11 @@ int cbx_solve_record(cbx_network* net, const cbx_cell_params* phi, const double*
 
 int cbx_grad(cbx_tape* tape, const double* cot_x, void* stream, double* g_logalpha, double* g_lognH,
              double* g_T) {
+  return cbx_grad_env(tape, cot_x, stream, g_logalpha, g_lognH, g_T, nullptr, nullptr, nullptr);
+}
+
+int cbx_grad_env(cbx_tape* tape, const double* cot_x, void* stream, double* g_logalpha, double* g_lognH,
+                 double* g_T, double* g_lnzeta, double* g_lnG0, double* g_AV) {
   if (!tape) return fail(CBX_E_ARG, "tape is NULL");
   const int C = tape->recorded_C;
   if (C < 1) return fail(CBX_E_ARG, "nothing recorded on this tape");
@@ -423,6 +428,8 @@ int cbx_grad(cbx_tape* tape, const double* cot_x, void* stream, double* g_logalp
   e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
   if (e == cudaSuccess) e = (cudaError_t)launch_grad(a, grid, stream);
   if (e == cudaSuccess && g_logalpha) e = (cudaError_t)launch_reduce_cells(a.gcell, C, h.R, g_logalpha, stream);
+  if (e == cudaSuccess && (g_lnzeta || g_lnG0 || g_AV))
+    e = (cudaError_t)launch_env_grad(a.gcell, C, net->dev, g_lnzeta, g_lnG0, g_AV, stream);
   cudaError_t e2 = cudaFreeAsync(buf, st);
   if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
   if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync(adjoint workspace)");

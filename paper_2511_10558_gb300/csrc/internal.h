@@ -120,6 +120,9 @@ long long grad_workspace_doubles(int S, int R, int nnzJ);
 int grad_occupancy(int S, int R, int nseg);
 int launch_grad(const GradArgs& a, int grid, void* stream);
 int launch_reduce_cells(const double* gcell, int C, int R, double* out, void* stream);
+// Per-cell dL/d ln zeta, dL/d ln G0, dL/dA_V from gcell (outputs may be null).
+int launch_env_grad(const double* gcell, int C, const DevNet& n, double* g_lnzeta, double* g_lnG0, double* g_AV,
+                    void* stream);
 
 // Launch plan of the solver kernel for one network and precision: matrix in
 // shared memory (gm = false) or in the CTA's global workspace (gm = true).

@@ -1632,6 +1632,51 @@ __global__ void reduce_cells_kernel(const double* gcell, int C, int R, double* o
   out[j] = acc;
 }
 
+// Environment gradients of each cell from its per-reaction gradients
+// dL/d ln k_j (k_j is proportional to alpha_j, so these are the per-cell
+// dL/d ln alpha_j): cosmic-ray coefficients carry the factor zeta (Sec. 2) and
+// photo coefficients G0 exp(-gamma_j A_V) (App. B.1), hence
+//   dL/d ln zeta = sum over cosmic-ray j,  dL/d ln G0 = sum over photo j,
+//   dL/dA_V = -sum over photo j of gamma_j dL/d ln k_j.
+// One warp per cell: lanes take reactions lane, lane + 32, ..., and lane 0
+// ends with a fixed shuffle-tree sum (deterministic).
+__global__ void env_grad_kernel(const double* gcell, int C, int R, const int* rtype, const double* gamma,
+                                double* g_lnzeta, double* g_lnG0, double* g_AV) {
+  const int cell = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (cell >= C) return;  // whole warps leave together
+  const double* row = gcell + (size_t)cell * R;
+  double z = 0.0, g = 0.0, av = 0.0;
+  for (int j = lane; j < R; j += 32) {
+    const int t = rtype[j];
+    const double v = row[j];
+    if (t == CBX_COSMIC_RAY) {
+      z += v;
+    } else if (t == CBX_PHOTO) {
+      g += v;
+      av -= gamma[j] * v;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    z += __shfl_xor_sync(FULL, z, o);
+    g += __shfl_xor_sync(FULL, g, o);
+    av += __shfl_xor_sync(FULL, av, o);
+  }
+  if (lane == 0) {
+    if (g_lnzeta) g_lnzeta[cell] = z;
+    if (g_lnG0) g_lnG0[cell] = g;
+    if (g_AV) g_AV[cell] = av;
+  }
+}
+
+int launch_env_grad(const double* gcell, int C, const DevNet& n, double* g_lnzeta, double* g_lnG0, double* g_AV,
+                    void* stream) {
+  if (C <= 0) return cudaSuccess;
+  constexpr int kCellsPerBlock = 8;
+  env_grad_kernel<<<(C + kCellsPerBlock - 1) / kCellsPerBlock, 32 * kCellsPerBlock, 0, (cudaStream_t)stream>>>(
+      gcell, C, n.R, n.rtype, n.gamma, g_lnzeta, g_lnG0, g_AV);
+  return cudaGetLastError();
+}
+
 long long grad_workspace_doubles(int S, int R, int nnzJ) {
   (void)S;
   return (4LL * R + nnzJ + 31) / 32 * 32;

@@ -5,9 +5,11 @@
 * A + B -> C: derivatives of the closed form x_A(t) w.r.t. ln kappa, taken by
   complex-step differentiation of that closed form; the n_H gradient equals the
   ln alpha gradient and the T gradient is (beta/T + gamma/T^2) times it.
+* A -> B by a photo reaction: d x_B / d ln G0 and d x_B / dA_V from the
+  closed form (environment gradients).
 * A synthetic 32-species cell: the adjoint of the replayed (frozen
   step/order, exact corrector) map against central finite differences of the
-  same map, step 1e-6 in ln alpha, ln n_H and 1e-6 T in T.
+  same map, step 1e-6 in ln alpha, ln n_H, ln zeta, ln G0, A_V and 1e-6 T in T.
 """
 import numpy as np
 import pytest
@@ -28,6 +30,29 @@ def test_first_order_decay_sensitivity():
     g_la, g_nH, g_T = adj.adjoint(net, phi, [a, 1e-20], res.program, np.array([0.0, 1.0]))
     assert g_la[0] == pytest.approx(a * k * t * np.exp(-k * t), rel=1e-6)
     assert g_nH == 0.0 and g_T == 0.0
+    # k = alpha zeta: the zeta sensitivity is the same closed form; no photo terms
+    g_z, g_g0, g_av = adj.environment_gradients(net, g_la)
+    assert g_z == pytest.approx(a * k * t * np.exp(-k * t), rel=1e-6)
+    assert g_g0 == 0.0 and g_av == 0.0
+
+
+def test_photo_decay_environment_sensitivity():
+    # A -> B by a photo reaction, k = alpha G0 exp(-gamma A_V): x_B = a (1 - exp(-k t)),
+    # d x_B / d ln G0 = a k t exp(-k t), d x_B / dA_V = -gamma a k t exp(-k t)
+    gam = 2.0
+    net = tiny(2, [(synth.PHOTO, (0,), (1,), 1e-9, 0, gam)])
+    phi = [1e4, 20.0, 1.5, 3.0, 1.3e-17]
+    k = chem.rate_coefficients(net, phi)[0]
+    assert k == pytest.approx(1e-9 * 3.0 * np.exp(-gam * 1.5), rel=1e-15)
+    t = 1.5 / k
+    a = 1e-3
+    res = bdf.solve_cell(net, phi, np.array([a, 1e-20]), 0.0, t, 1e-10, 1e-30, record=True)
+    g_la, _, _ = adj.adjoint(net, phi, [a, 1e-20], res.program, np.array([0.0, 1.0]))
+    g_z, g_g0, g_av = adj.environment_gradients(net, g_la)
+    exact = a * k * t * np.exp(-k * t)
+    assert g_z == 0.0
+    assert g_g0 == pytest.approx(exact, rel=1e-6)
+    assert g_av == pytest.approx(-gam * exact, rel=1e-6)
 
 
 def test_second_order_sensitivity():
@@ -90,6 +115,17 @@ def test_adjoint_matches_frozen_finite_differences(net32):
     p_p[1] += eps * phi[1]
     p_m[1] -= eps * phi[1]
     assert (loss(p=p_p) - loss(p=p_m)) / (2 * eps * phi[1]) == pytest.approx(g_T, rel=1e-3)
+    # environment: ln zeta (phi[4]), ln G0 (phi[3]), A_V (phi[2])
+    g_z, g_g0, g_av = adj.environment_gradients(net32, g_la)
+    for col, g_env in ((4, g_z), (3, g_g0)):
+        p_p, p_m = phi.copy(), phi.copy()
+        p_p[col] *= np.exp(eps)
+        p_m[col] *= np.exp(-eps)
+        assert (loss(p=p_p) - loss(p=p_m)) / (2 * eps) == pytest.approx(g_env, rel=1e-3), col
+    p_p, p_m = phi.copy(), phi.copy()
+    p_p[2] += eps
+    p_m[2] -= eps
+    assert (loss(p=p_p) - loss(p=p_m)) / (2 * eps) == pytest.approx(g_av, rel=1e-3)
 
 
 def test_adjoint_of_adaptive_run_close_to_replayed(net32):
