@@ -609,6 +609,55 @@ def run_zeta(args):
     print(json.dumps(res), flush=True)
 
 
+def run_track(args):
+    """Time-dependent environment phi(t) (the generalised system of Sec. 2 with phi a function
+    of time): 150 sp, 4096 seeded cells, each on a collapse-and-warming track (n_H x10, T x1.5,
+    A_V +5 mag over 1 Myr, 4 knots); FP64 and mixed cell-solves/s next to the same cells at
+    constant phi, and sampled cells against the oracle's solve_cell_track."""
+    torch, dev, carbox = _gpu_setup()
+    from oracle import bdf
+    stream = torch.cuda.current_stream(dev)
+    net = synth.make_network(S_SP, R_RX)
+    N = carbox.Network.from_synth(net)
+    C = 4096
+    phi_h = synth.cells(C)
+    tr_h = synth.tracks(phi_h, T_END)
+    x0_h = np.repeat(synth.initial_abundances(net)[:, None], C, axis=1)
+    phi = torch.tensor(phi_h, device=dev).contiguous()
+    tr = torch.tensor(tr_h, device=dev).contiguous()
+    x0 = torch.tensor(x0_h, device=dev).contiguous()
+    res = {"config": "track", "workload": f"{S_SP} species / {R_RX} reactions, {C} cells, 0 -> 1 Myr, rtol 1e-4, "
+                                          "atol 1e-20; tracks: n_H x10 (geometric), T x1.5, A_V +5 mag, 4 knots"}
+    for name, prec in (("fp64", carbox.CBX_FP64), ("mixed", carbox.CBX_MIXED)):
+        o = carbox.options(rtol=RTOL, atol=ATOL, precision=prec)
+        out = {}
+        for kind in ("track", "constant"):
+            run = (lambda: carbox.solve_track(N, tr, x0, 0.0, T_END, o)) if kind == "track" else \
+                  (lambda: carbox.solve(N, phi, x0, 0.0, T_END, o))
+            run()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            x, st, _ = run()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            out[kind] = {"ms": ms, "value": C / (ms / 1e3), "unit": "cell-solves/s",
+                         "cells_ok": int((st == 0).sum().item())}
+            if kind == "track":
+                xt = x.cpu().numpy()
+        out["track_over_constant_time"] = out["track"]["ms"] / out["constant"]["ms"]
+        res[name] = out
+        if name == "fp64":
+            checks = []
+            for c in [0, 7]:
+                ref = bdf.solve_cell_track(net, tr_h[c], x0_h[:, c], 0.0, T_END, RTOL, ATOL).x
+                big = ref > 1e-12
+                checks.append({"cell": c, "max_rel_vs_oracle": float(np.max(np.abs(xt[big, c] / ref[big] - 1)))})
+            res["checks_fp64"] = checks
+    print(json.dumps(res), flush=True)
+
+
 def run_serving(args):
     """Config 5: Poisson requests over 32/150/500-species networks through cbx_server."""
     torch, dev, carbox = _gpu_setup()
@@ -680,7 +729,7 @@ def main():
     ap.add_argument("--only", choices=["fp64", "mixed"], default=None)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-large", action="store_true")
-    ap.add_argument("--config", choices=["bench", "large", "adjoint", "serving", "zeta"], default="bench")
+    ap.add_argument("--config", choices=["bench", "large", "adjoint", "serving", "zeta", "track"], default="bench")
     ap.add_argument("--duration", type=float, default=2.0, help="serving: seconds of Poisson arrivals")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean requests per second")
     args = ap.parse_args()
@@ -694,6 +743,8 @@ def main():
         run_serving(args)
     elif args.config == "zeta":
         run_zeta(args)
+    elif args.config == "track":
+        run_track(args)
     else:
         run_gpu(args)
 

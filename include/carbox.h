@@ -185,6 +185,26 @@ int cbx_solve(cbx_network* net, const cbx_cell_params* phi, const double* x0, in
               cbx_cell_stats* stats);
 
 /*
+ * cbx_solve with a time-dependent environment phi(t) per cell (Sec. 2 writes
+ * the system as dn/dt = f(n, k(phi), phi); here phi follows a track): the
+ * rate coefficients are re-evaluated at every time at which the method
+ * evaluates f or J (the step's t_new, and t0 and t0 + h0 at the start).
+ *   track [C][K][6]  device pointer, per cell K knots (t_k, n_H, T, A_V, G0,
+ *                    zeta), t_k in seconds and strictly increasing; phi(t) is
+ *                    linear between knots and takes the end values outside
+ *                    [t_0, t_{K-1}]. x is per n_H, so a changing n_H enters
+ *                    only the two-body coefficients.
+ *   K >= 1           (K = 1: a constant phi, the same result as cbx_solve).
+ * Other arguments, ownership and results as for cbx_solve. A cell with a
+ * non-finite knot, n_H or T <= 0 at a knot, or knot times not increasing ends
+ * with CBX_CELL_BAD_INPUT without touching the others.
+ * Errors: those of cbx_solve, and CBX_E_ARG for K < 1 or a NULL track.
+ */
+int cbx_solve_track(cbx_network* net, const double* track, int K, const double* x0, int C, double t0,
+                    double t_end, const cbx_options* opt, void* stream, double* x_out, int* cell_status,
+                    cbx_cell_stats* stats);
+
+/*
  * As cbx_solve, with HOST pointers for phi, x0, x_out, cell_status and stats:
  * the call copies the inputs to the device, solves, copies the results back
  * and synchronises `stream` before returning.

@@ -286,3 +286,39 @@ def solve_cell(net, phi, x0, t0, t_end, rtol, atol, max_steps=100000, record=Fal
     return integrate(lambda t, y: chem.rhs(net, kappa, y, nu),
                      lambda t, y: chem.jacobian(net, kappa, y, nu),
                      t0, np.asarray(x0, dtype=float), t_end, rtol, atol, max_steps, record)
+
+
+def track_params(track, t):
+    """phi(t) = (n_H, T, A_V, G0, zeta) of one cell from its knots [K, 6]
+    (t_k, n_H, T, A_V, G0, zeta): linear between knots, the end values
+    outside [t_0, t_{K-1}] (the environment phi of the generalised system
+    dn/dt = f(n, k(phi), phi) of Sec. 2, here a function of time)."""
+    track = np.asarray(track, dtype=float)
+    K = track.shape[0]
+    k = 0
+    while k + 1 < K and track[k + 1, 0] <= t:
+        k += 1
+    A = track[k]
+    if k + 1 >= K or t <= A[0]:
+        return A[1:].copy()
+    B = track[k + 1]
+    w = (t - A[0]) / (B[0] - A[0])
+    return A[1:] + w * (B[1:] - A[1:])
+
+
+def solve_cell_track(net, track, x0, t0, t_end, rtol, atol, max_steps=100000, record=False):
+    """Integrate one cell whose environment follows `track`: the rate
+    coefficients are those of phi(t) at every time the method evaluates f or J.
+    x is per n_H, so a changing n_H enters only the two-body coefficients."""
+    nu = chem.stoichiometry(net)
+    last = {}
+
+    def kappa(t):
+        if last.get("t") != t:
+            last["t"] = t
+            last["k"] = chem.effective_coefficients(net, track_params(track, t))
+        return last["k"]
+
+    return integrate(lambda t, y: chem.rhs(net, kappa(t), y, nu),
+                     lambda t, y: chem.jacobian(net, kappa(t), y, nu),
+                     t0, np.asarray(x0, dtype=float), t_end, rtol, atol, max_steps, record)

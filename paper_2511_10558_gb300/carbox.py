@@ -98,6 +98,8 @@ def _load():
                                        P, P]),
         "cbx_grad": (C.c_int, [P, P, P, P, P, P]),
         "cbx_grad_env": (C.c_int, [P, P, P, P, P, P, P, P, P]),
+        "cbx_solve_track": (C.c_int, [P, P, C.c_int, P, C.c_int, C.c_double, C.c_double, C.POINTER(cbx_options), P,
+                                      P, P, P]),
         "cbx_tape_program": (C.c_int, [P, C.c_int, P, P, P, C.c_int]),
         "cbx_server_create": (C.c_int, [C.c_size_t, C.c_int, C.c_int, C.POINTER(P)]),
         "cbx_server_submit": (C.c_int, [P, P, P, P, C.c_int, C.c_double, C.c_double, C.POINTER(cbx_options),
@@ -213,6 +215,29 @@ def solve(net, phi, x0, t0, t_end, opt=None, stream=None, x_out=None, status=Non
     o = opt if opt is not None else options()
     check(lib.cbx_solve(net.handle, _ptr(phi), _ptr(x0), Cn, float(t0), float(t_end), C.byref(o),
                         C.c_void_p(stream.cuda_stream), _ptr(x_out), _ptr(status), _ptr(stats)), "cbx_solve")
+    return x_out, status, stats
+
+
+def solve_track(net, track, x0, t0, t_end, opt=None, stream=None, stats=None):
+    """cbx_solve_track on torch CUDA tensors: track [C, K, 6] f64 knots (t, n_H, T, A_V,
+    G0, zeta), x0 [S, C] f64. Returns (x_out [S, C], status [C] int32, stats or None)."""
+    import torch
+    assert track.is_cuda and track.dtype == torch.float64 and track.is_contiguous() and track.dim() == 3
+    assert track.shape[2] == 6
+    Cn, K = int(track.shape[0]), int(track.shape[1])
+    assert x0.is_cuda and x0.dtype == torch.float64 and x0.is_contiguous() and tuple(x0.shape) == (net.S, Cn)
+    dev = track.device
+    if stats is not None:
+        assert (stats.is_cuda and stats.dtype == torch.int32 and stats.is_contiguous()
+                and tuple(stats.shape) == (Cn, STATS_INTS)), "stats must be stats_tensor(C, device)"
+    x_out = torch.empty((net.S, Cn), dtype=torch.float64, device=dev)
+    status = torch.empty(Cn, dtype=torch.int32, device=dev)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    o = opt if opt is not None else options()
+    check(lib.cbx_solve_track(net.handle, _ptr(track), K, _ptr(x0), Cn, float(t0), float(t_end), C.byref(o),
+                              C.c_void_p(stream.cuda_stream), _ptr(x_out), _ptr(status), _ptr(stats)),
+          "cbx_solve_track")
     return x_out, status, stats
 
 

@@ -196,10 +196,11 @@ int cbx_network_info(const cbx_network* net, cbx_netinfo* out) {
 
 static int solve_impl(cbx_network* net, const cbx_cell_params* phi, const double* x0, int C, double t0,
                       double t_end, const cbx_options* opt, void* stream, double* x_out, int* cell_status,
-                      cbx_cell_stats* stats, cbx_tape* tape, int max_grid = 0) {
+                      cbx_cell_stats* stats, cbx_tape* tape, int max_grid = 0, const double* track = nullptr,
+                      int K = 0) {
   if (!net) return fail(CBX_E_ARG, "net is NULL");
   if (C < 0) return fail(CBX_E_ARG, "C must be >= 0");
-  if (C > 0 && (!phi || !x0 || !x_out || !cell_status)) return fail(CBX_E_ARG, "NULL array with C > 0");
+  if (C > 0 && ((!phi && !track) || !x0 || !x_out || !cell_status)) return fail(CBX_E_ARG, "NULL array with C > 0");
   if (!std::isfinite(t0) || !std::isfinite(t_end) || t_end < t0) return fail(CBX_E_ARG, "need finite t0 <= t_end");
   cbx_options o;
   cbx_default_options(&o);
@@ -225,6 +226,8 @@ static int solve_impl(cbx_network* net, const cbx_cell_params* phi, const double
   SolveArgs a{};
   a.net = net->dev;
   a.phi = phi;
+  a.track = track;
+  a.K = K;
   a.x0 = x0;
   a.C = C;
   a.t0 = t0;
@@ -274,6 +277,13 @@ int cbx_solve(cbx_network* net, const cbx_cell_params* phi, const double* x0, in
               double t_end, const cbx_options* opt, void* stream, double* x_out, int* cell_status,
               cbx_cell_stats* stats) {
   return solve_impl(net, phi, x0, C, t0, t_end, opt, stream, x_out, cell_status, stats, nullptr);
+}
+
+int cbx_solve_track(cbx_network* net, const double* track, int K, const double* x0, int C, double t0, double t_end,
+                    const cbx_options* opt, void* stream, double* x_out, int* cell_status, cbx_cell_stats* stats) {
+  if (K < 1) return fail(CBX_E_ARG, "K must be >= 1");
+  if (C > 0 && !track) return fail(CBX_E_ARG, "track is NULL");
+  return solve_impl(net, nullptr, x0, C, t0, t_end, opt, stream, x_out, cell_status, stats, nullptr, 0, track, K);
 }
 
 int cbx_solve_host(cbx_network* net, const cbx_cell_params* phi, const double* x0, int C, double t0,

@@ -96,6 +96,8 @@ struct SolveArgs {
   long long ws_stride;
   int* counter;    // next-cell counter, zero before the launch
   int piv_ints;    // pivot-list ints staged in shared memory (set by launch_solver)
+  const double* track;  // [C][K][6] (t, n_H, T, A_V, G0, zeta) knots, or null: phi is constant
+  int K;
 };
 
 struct GradArgs {

@@ -1141,6 +1141,35 @@ __device__ void rec_step(const SolveArgs& a, int cell, Recorder& r, int q, doubl
   r.nsteps++;
 }
 
+// Environment of a cell at time t from its track (t_k, n_H, T, A_V, G0, zeta),
+// k = 0..K-1: linear between knots, the end values outside [t_0, t_{K-1}]
+// (the phi(t) of the generalised system of Sec. 2; x is per n_H, so a
+// changing n_H enters only the two-body coefficients).
+__device__ cbx_cell_params track_params(const SolveArgs& a, int cell, double t) {
+  const double* k0 = a.track + (size_t)cell * a.K * 6;
+  int k = 0;
+  while (k + 1 < a.K && k0[(k + 1) * 6] <= t) ++k;
+  const double* A = k0 + k * 6;
+  if (k + 1 >= a.K || t <= A[0]) return cbx_cell_params{A[1], A[2], A[3], A[4], A[5]};
+  const double* B = A + 6;
+  const double w = (t - A[0]) / (B[0] - A[0]);
+  return cbx_cell_params{fma(w, B[1] - A[1], A[1]), fma(w, B[2] - A[2], A[2]), fma(w, B[3] - A[3], A[3]),
+                         fma(w, B[4] - A[4], A[4]), fma(w, B[5] - A[5], A[5])};
+}
+
+// Every knot finite with n_H, T > 0, and the knot times strictly increasing.
+__device__ bool track_valid(const SolveArgs& a, int cell) {
+  const double* k0 = a.track + (size_t)cell * a.K * 6;
+  for (int k = 0; k < a.K; ++k) {
+    const double* A = k0 + k * 6;
+    for (int f = 0; f < 6; ++f)
+      if (!isfinite(A[f])) return false;
+    if (!(A[1] > 0.0) || !(A[2] > 0.0)) return false;
+    if (k > 0 && !(A[0] > A[-6])) return false;
+  }
+  return true;
+}
+
 template <typename LT, bool GM>
 __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
   const DevNet& n = a.net;
@@ -1154,19 +1183,28 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
     c.st->t_begin_ns = (long long)globaltimer();
   }
   int attempts = 0;
-  const cbx_cell_params p = a.phi[cell];
+  const cbx_cell_params p = a.track ? track_params(a, cell, a.t0) : a.phi[cell];
   int status = CBX_CELL_OK;
   Recorder rec;
   rec.on = a.tape.nops != nullptr;
   for (int i = threadIdx.x; i < S; i += NT) s.y[i] = a.x0[(size_t)__ldg(n.perm + i) * a.C + cell];
   if (!(p.n_H > 0.0) || !(p.T > 0.0) || !isfinite(p.n_H) || !isfinite(p.T) || !isfinite(p.A_V) ||
-      !isfinite(p.G0) || !isfinite(p.zeta)) {
+      !isfinite(p.G0) || !isfinite(p.zeta) || (a.track && !track_valid(a, cell))) {
     status = CBX_CELL_BAD_INPUT;
     __syncthreads();
     for (int i = threadIdx.x; i < S; i += NT) a.x_out[(size_t)__ldg(n.perm + i) * a.C + cell] = s.y[i];
   } else {
     rate_coefficients(n, p, c.kap);
     __syncthreads();
+    // with a track, the coefficients follow phi(t) to every time f or J is evaluated at
+    double t_rates = a.t0;
+    auto rates_at = [&](double tt) {
+      if (a.track && tt != t_rates) {
+        rate_coefficients(n, track_params(a, cell, tt), c.kap);
+        __syncthreads();
+        t_rates = tt;
+      }
+    };
     const double rtol = a.rtol, atol = a.atol, t_end = a.t_end;
     double* D = s.D;
     // f0 and the initial step (Hairer, Norsett & Wanner I, II.4, p = 1)
@@ -1179,6 +1217,7 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
     const double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
     for (int i = threadIdx.x; i < S; i += NT) s.tmp[i] = s.y[i] + h0 * s.f[i];
     __syncthreads();
+    rates_at(a.t0 + h0);
     rhs(n, c.kap, s.tmp, s.dy, s.r, s.part);
     if (threadIdx.x == 0) c.st->rhs_evals++;
     for (int i = threadIdx.x; i < S; i += NT) s.tmp[i] = s.dy[i] - s.f[i];
@@ -1194,6 +1233,7 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
       for (int r = 2; r < kDiffRows; ++r) D[r * S + i] = 0.0;
     }
     rec_op(a, cell, rec, kOpInit, 1, h);
+    rates_at(a.t0);
     jacobian(n, c.kap, s.y, c.g, c.Jv);
     if (threadIdx.x == 0) c.st->jac_evals++;
     int q = 1, n_equal = 0;
@@ -1235,6 +1275,7 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
         const double cc = h / gq;
         bool conv = false;
         int iters = 0;
+        rates_at(t_new);
         for (;;) {
           if (!lu_valid) {
             factor(c, cc);

@@ -334,3 +334,22 @@ def initial_abundances(net: Network) -> np.ndarray:
     x[net.index("N")] = 7.5e-5
     x[net.index("e-")] = 1e-4
     return x
+
+
+def tracks(phi: np.ndarray, t_end: float, n_knots: int = 4) -> np.ndarray:
+    """Environment tracks [C, K, 6] (t, n_H, T, A_V, G0, zeta) for the cells phi [C, 5]:
+    a collapse with warming over [0, t_end] -- n_H rising tenfold, T by half again,
+    A_V by 5 mag -- at K knots equally spaced in time (G0 and zeta held). The knot
+    values follow s = (k / (K-1)) on a geometric path for n_H, linear for T and A_V."""
+    phi = np.asarray(phi, dtype=float)
+    C = phi.shape[0]
+    out = np.empty((C, n_knots, 6))
+    for k in range(n_knots):
+        s = k / (n_knots - 1) if n_knots > 1 else 0.0
+        out[:, k, 0] = s * t_end
+        out[:, k, 1] = phi[:, 0] * 10.0 ** s
+        out[:, k, 2] = phi[:, 1] * (1.0 + 0.5 * s)
+        out[:, k, 3] = phi[:, 2] + 5.0 * s
+        out[:, k, 4] = phi[:, 3]
+        out[:, k, 5] = phi[:, 4]
+    return out

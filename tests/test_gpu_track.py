@@ -1,0 +1,94 @@
+"""Time-dependent environment phi(t) (cbx_solve_track) vs the oracle (GPU).
+
+* A constant track gives bitwise the constant-phi GPU solve.
+* A collapse-and-warming track: abundances within 1e-4 of the oracle's
+  solve_cell_track, or (on another step program) as accurate as the oracle
+  against an rtol-1e-8 reference; conservation on every cell.
+* A cell with knot times out of order ends BAD_INPUT without touching others;
+  K < 1 is an argument error.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import bdf, chem  # noqa: E402
+from paper_2511_10558_gb300 import build as _build  # noqa: E402
+
+_build.build()
+from paper_2511_10558_gb300 import carbox, synth  # noqa: E402
+
+YR = synth.YEAR
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def run_track(N, tr, x0, t_end, dev):
+    x, st, _ = carbox.solve_track(N, torch.tensor(tr, device=dev).contiguous(),
+                                  torch.tensor(x0, device=dev).contiguous(), 0.0, t_end)
+    torch.cuda.synchronize()
+    return x.cpu().numpy(), st.cpu().numpy()
+
+
+def test_constant_track_is_constant_phi(dev, net150):
+    C = 16
+    phi = synth.cells(C)
+    x0 = np.repeat(synth.initial_abundances(net150)[:, None], C, axis=1)
+    t_end = 1e5 * YR
+    N = carbox.Network.from_synth(net150)
+    xr, sr, _ = carbox.solve(N, torch.tensor(phi, device=dev), torch.tensor(x0, device=dev).contiguous(), 0.0, t_end)
+    tr = np.concatenate([np.zeros((C, 1, 1)), phi[:, None, :]], axis=2)  # K = 1
+    x, st = run_track(N, tr, x0, t_end, dev)
+    np.testing.assert_array_equal(x, xr.cpu().numpy())
+    np.testing.assert_array_equal(st, sr.cpu().numpy())
+
+
+def test_collapse_track_matches_oracle(dev, net150):
+    C = 40
+    t_end = 1e6 * YR
+    phi = synth.cells(C)
+    tr = synth.tracks(phi, t_end)
+    x0 = np.repeat(synth.initial_abundances(net150)[:, None], C, axis=1)
+    N = carbox.Network.from_synth(net150)
+    x, st = run_track(N, tr, x0, t_end, dev)
+    assert np.all(st == carbox.CBX_CELL_OK)
+    for c in range(C):
+        E0, Q0 = chem.element_totals(net150, x0[:, c])
+        E1, Q1 = chem.element_totals(net150, x[:, c])
+        assert np.all(np.abs(E1 - E0) <= 1e-10 * E0)
+    # the track changes the answer (it is not ignored)
+    xc, _, _ = carbox.solve(N, torch.tensor(phi, device=dev), torch.tensor(x0, device=dev).contiguous(), 0.0, t_end)
+    assert np.max(np.abs(xc.cpu().numpy()[:, 0] / x[:, 0] - 1)) > 1e-2
+    for c in [0, 7]:
+        ref = bdf.solve_cell_track(net150, tr[c], x0[:, c], 0.0, t_end, 1e-4, 1e-20).x
+        big = ref > 1e-12
+        rel = np.max(np.abs(x[big, c] / ref[big] - 1))
+        if rel <= 1e-4:
+            continue
+        tight = bdf.solve_cell_track(net150, tr[c], x0[:, c], 0.0, t_end, 1e-8, 1e-26).x
+        big = tight > 1e-12
+        e_gpu = np.max(np.abs(x[big, c] / tight[big] - 1))
+        e_orc = np.max(np.abs(ref[big] / tight[big] - 1))
+        assert e_gpu <= 2 * max(e_orc, 1e-3), (c, rel, e_gpu, e_orc)
+
+
+def test_bad_track_and_arguments(dev, net32):
+    phi = np.repeat(synth.one_cell(), 3, axis=0)
+    t_end = 1e4 * YR
+    tr = synth.tracks(phi, t_end)
+    tr[1, 2, 0] = tr[1, 1, 0]  # knot times not increasing in cell 1
+    x0 = np.repeat(synth.initial_abundances(net32)[:, None], 3, axis=1)
+    N = carbox.Network.from_synth(net32)
+    x, st = run_track(N, tr, x0, t_end, dev)
+    assert st[1] == carbox.CBX_CELL_BAD_INPUT and st[0] == carbox.CBX_CELL_OK and st[2] == carbox.CBX_CELL_OK
+    np.testing.assert_array_equal(x[:, 1], x0[:, 1])
+    np.testing.assert_array_equal(x[:, 0], x[:, 2])
+    with pytest.raises(RuntimeError):
+        carbox.solve_track(N, torch.zeros((3, 0, 6), dtype=torch.float64, device=dev),
+                           torch.tensor(x0, device=dev).contiguous(), 0.0, t_end)
