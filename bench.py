@@ -292,7 +292,8 @@ def run_gpu(args):
         ms64 = timed(carbox.CBX_FP64, args.steps, args.warmup) if args.only != "mixed" else [float("nan")]
     st64 = carbox.stats_dict(stats.cpu().numpy())
     ok64 = int((status == 0).sum().item())
-    x64_sample = x_out[:, :max(args.ref_cells, os.cpu_count() or 1)].cpu().numpy()
+    n_sample = min(CELLS, max(args.ref_cells, os.cpu_count() or 1))  # the oracle sample (cpu_baseline)
+    x64_sample = x_out[:, :n_sample].cpu().numpy()
     t_max = max_over_ranks(sum(ms64) / 1e3, dev)
     value = weak_value(ws, CELLS, args.steps, t_max)
     ms_per_step = 1e3 * t_max / args.steps
@@ -312,7 +313,7 @@ def run_gpu(args):
         return
     stmx = carbox.stats_dict(stats.cpu().numpy())
     okmx = int((status == 0).sum().item())
-    xmx_sample = x_out[:, :max(args.ref_cells, os.cpu_count() or 1)].cpu().numpy()
+    xmx_sample = x_out[:, :n_sample].cpu().numpy()
     mixed_value = CELLS * len(msmx) / (sum(msmx) / 1e3)
     latmx = (stmx["t_end_ns"] - stmx["t_begin_ns"]) / 1e6
 
@@ -337,7 +338,7 @@ def run_gpu(args):
     cpu = parity = None
     if ws == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
-        ncell = max(cores, args.ref_cells)
+        ncell = n_sample
         v, dt, x_ref = time_oracle(ncell, cores)
         cpu = {"value": v, "unit": "cell-solves/s", "cores": cores, "kind": "oracle",
                "sample": f"first {ncell} of the {CELLS} seeded cells, spawn pool of {cores} processes, {dt:.1f} s"}
