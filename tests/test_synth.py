@@ -63,3 +63,16 @@ def test_initial_abundances(net32):
     x = synth.initial_abundances(net32)
     assert x[net32.index("H2")] == 0.5 and x[net32.index("e-")] == x[net32.index("C+")]
     assert np.sum(x == 1e-20) == net32.n_species - 6
+
+
+def test_tracks_recipe():
+    phi = synth.cells(5)
+    t_end = 1e6 * synth.YEAR
+    tr = synth.tracks(phi, t_end)
+    assert tr.shape == (5, 4, 6)
+    assert np.all(np.diff(tr[:, :, 0], axis=1) > 0) and tr[0, -1, 0] == t_end
+    np.testing.assert_allclose(tr[:, 0, 1:], phi)                       # starts at the cell's phi
+    np.testing.assert_allclose(tr[:, -1, 1], 10.0 * phi[:, 0])           # n_H x10
+    np.testing.assert_allclose(tr[:, -1, 2], 1.5 * phi[:, 1])            # T x1.5
+    np.testing.assert_allclose(tr[:, -1, 3], phi[:, 2] + 5.0)            # A_V + 5 mag
+    np.testing.assert_array_equal(tr[:, :, 4:], np.repeat(phi[:, None, 3:], 4, axis=1))
