@@ -25,11 +25,13 @@ One step, order q, size h:
 Constants and policies (the CUDA path restates the same values on its own):
     norms        weighted RMS with weights 1/(atol + rtol |y_i|): the Newton
                  test uses |y| of the predictor, the error test |y| of the result
-    Newton       at most 4 iterations; the contraction rate is
-                 rate_k = ||dy_k|| / ||dy_{k-1}||; stop with failure when
-                 rate >= 1 or rate^(4-k) / (1-rate) ||dy_k|| > tol_N; converged
-                 when ||dy|| = 0 or rate / (1-rate) ||dy|| < tol_N, with
-                 tol_N = max(10 eps / rtol, min(0.03, sqrt(rtol)))
+    Newton       simplified Newton, at most 4 increments, with the stopping
+                 rules of Hairer & Wanner II, Sec. IV.8 (contraction factor
+                 from successive increment norms, geometric-tail error bound;
+                 see newton_corrector), tolerance
+                 tol_N = max(10 eps / rtol, min(0.03, sqrt(rtol))): a small
+                 fraction of the error test's unit scale, never below the
+                 rounding level of the weighted norm
     Jacobian     evaluated at (t0, y0), and again at the predictor when Newton
                  fails with a Jacobian that is not current (it is current only
                  between its evaluation and the next accepted step)
@@ -80,8 +82,19 @@ def wrms(v, scale):
     return float(np.sqrt(np.mean((v / scale) ** 2)))
 
 
-def initial_step(f, t0, y0, f0, t_end, rtol, atol):
-    """Starting step of Hairer, Norsett & Wanner I, Sec. II.4, for order p = 1."""
+def initial_step(f, t0, y0, f0, t_end, rtol, atol, order=1):
+    """Starting step of Hairer, Norsett & Wanner, Solving ODEs I, Sec. II.4
+    ("Starting step size"), for a method of order p = `order` (the BDF starts
+    at order 1). Norms are weighted RMS with scale atol + rtol |y0|:
+      (a) d0 = |y0|, d1 = |f0|;
+      (b) a first guess h0 = 0.01 d0 / d1 (1e-6 when d0 or d1 < 1e-5);
+      (c) one explicit Euler step y1 = y0 + h0 f0, and f1 = f(t0 + h0, y1);
+      (d) d2 = |f1 - f0| / h0, an estimate of the second derivative;
+      (e) h1 from 0.01 = h1^(p+1) max(d1, d2), i.e.
+          h1 = (0.01 / max(d1, d2))^(1/(p+1)), or max(1e-6, 1e-3 h0) when
+          max(d1, d2) <= 1e-15;
+      (f) h = min(100 h0, h1), here also capped at t_end - t0.
+    """
     scale = atol + rtol * np.abs(y0)
     d0 = wrms(y0, scale)
     d1 = wrms(f0, scale)
@@ -89,10 +102,8 @@ def initial_step(f, t0, y0, f0, t_end, rtol, atol):
     y1 = y0 + h0 * f0
     f1 = f(t0 + h0, y1)
     d2 = wrms(f1 - f0, scale) / h0
-    if max(d1, d2) <= 1e-15:
-        h1 = max(1e-6, h0 * 1e-3)
-    else:
-        h1 = (0.01 / max(d1, d2)) ** 0.5
+    dmax = max(d1, d2)
+    h1 = max(1e-6, h0 * 1e-3) if dmax <= 1e-15 else (0.01 / dmax) ** (1.0 / (order + 1))
     return min(100.0 * h0, h1, t_end - t0)
 
 
@@ -135,30 +146,51 @@ def rescale_differences(D, q, rho):
 
 
 def newton_corrector(fun, t_new, y_pred, c, psi, lu, scale, tol, maxiter=NEWTON_MAXITER):
-    """Simplified Newton on d - c f(y0 + d) + psi = 0 with a fixed LU of I - cJ."""
+    """Solve the corrector equation G(d) = d - c f(t_new, y_pred + d) + psi = 0
+    by simplified Newton: the matrix I - c J stays frozen (its LU is `lu`).
+
+    Iteration m = 1, 2, ..., maxiter computes the increment
+        Delta_m = (I - c J)^{-1} (-G(d_{m-1})),   d_0 = 0,
+    and its weighted RMS norm n_m. The stopping rules are those of Hairer &
+    Wanner, Solving ODEs II, Sec. IV.8 (simplified Newton for implicit
+    methods), which assume the iterates contract linearly:
+
+      * from m = 2 on, the contraction factor is estimated as
+        theta = n_m / n_{m-1} (increment m = 1 gives no estimate);
+      * with a factor theta < 1 the distance of d_m = d_{m-1} + Delta_m to
+        the solution is at most the geometric tail theta / (1 - theta) n_m:
+        d_m is accepted when that bound is below `tol` (or n_m is exactly 0);
+      * the iteration is abandoned, before Delta_m is applied, when
+        theta >= 1 (no contraction), or when the bound expected after the
+        last permitted increment, theta^(maxiter - m + 1) / (1 - theta) n_m
+        (maxiter - m further contractions of the tail), still exceeds `tol`;
+      * a non-finite right-hand side also abandons the iteration.
+
+    The iterate y = y_pred + d is carried as its own running sum (each
+    increment added to y and to d), so y is never re-formed from y_pred + d.
+
+    Returns (converged, increments computed, y, d).
+    """
     d = np.zeros_like(y_pred)
-    y = y_pred.copy()
-    dy_norm_old = None
-    converged = False
-    n_iter = 0
-    for k in range(maxiter):
-        n_iter = k + 1
+    y = np.array(y_pred, dtype=float)
+    n_prev = None  # norm of the previous increment
+    for m in range(1, maxiter + 1):
         f = fun(t_new, y)
         if not np.all(np.isfinite(f)):
-            break
-        dy = scipy.linalg.lu_solve(lu, c * f - psi - d)
-        dy_norm = wrms(dy, scale)
-        rate = None if dy_norm_old is None else dy_norm / dy_norm_old
-        if rate is not None and (rate >= 1.0 or
-                                 rate ** (maxiter - k) / (1.0 - rate) * dy_norm > tol):
-            break
-        y = y + dy
-        d = d + dy
-        if dy_norm == 0.0 or (rate is not None and rate / (1.0 - rate) * dy_norm < tol):
-            converged = True
-            break
-        dy_norm_old = dy_norm
-    return converged, n_iter, y, d
+            return False, m, y, d
+        delta = scipy.linalg.lu_solve(lu, c * f - psi - d)
+        n_m = wrms(delta, scale)
+        theta = None if n_prev is None else n_m / n_prev
+        if theta is not None:
+            hopeless = theta >= 1.0 or theta ** (maxiter - m + 1) / (1.0 - theta) * n_m > tol
+            if hopeless:
+                return False, m, y, d
+        y = y + delta
+        d = d + delta
+        if n_m == 0.0 or (theta is not None and theta / (1.0 - theta) * n_m < tol):
+            return True, m, y, d
+        n_prev = n_m
+    return False, maxiter, y, d
 
 
 class Result:
