@@ -1,6 +1,6 @@
 """Build libcarbox.so (sm_103a) in-tree with nvcc; no cmake, no torch extension.
 
-``build()`` compiles the three translation units in parallel and links them
+``build()`` compiles the translation units in parallel and links them
 into ``paper_2511_10558_gb300/lib/libcarbox.so``. It is skipped when the
 library is newer than every source.
 """
@@ -16,7 +16,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "lib", "libcarbox.so")
-SOURCES = ["solver.cu", "network.cpp", "capi.cpp", "noalloc.cu", "server.cpp"]
+SOURCES = ["solve_fp64.cu", "solve_fp64_gm.cu", "solve_mixed.cu", "solve_mixed_gm.cu", "adjoint.cu", "plan.cu",
+           "network.cpp", "capi.cpp", "noalloc.cu", "server.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -35,7 +36,7 @@ def source_hash() -> str:
     """Hash of the kernel sources (identifies the build a profile was taken on)."""
     import hashlib
     h = hashlib.sha256()
-    for f in sorted(SOURCES) + ["internal.h"]:
+    for f in sorted(SOURCES) + ["internal.h", "solver_dev.cuh"]:
         h.update(open(os.path.join(CSRC, f), "rb").read())
     h.update(open(os.path.join(INCLUDE, "carbox.h"), "rb").read())
     return h.hexdigest()[:16]

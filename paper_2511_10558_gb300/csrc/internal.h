@@ -140,6 +140,15 @@ long long workspace_doubles(int S, int R, int nnzJ, bool mixed, bool gm);
 SolverPlan plan_solver(int S, int R, int nseg, int nnzJ, bool mixed, int head_ints);
 // Launch the solver; returns a cudaError_t value.
 int launch_solver(const SolveArgs& a, const SolverPlan& p, int grid, void* stream);
+// One translation unit per kernel instantiation (precision x matrix placement).
+int launch_solve_fp64(const SolveArgs& a, size_t smem, int grid, void* stream);
+int launch_solve_fp64_gm(const SolveArgs& a, size_t smem, int grid, void* stream);
+int launch_solve_mixed(const SolveArgs& a, size_t smem, int grid, void* stream);
+int launch_solve_mixed_gm(const SolveArgs& a, size_t smem, int grid, void* stream);
+int occupancy_solve_fp64(size_t smem);
+int occupancy_solve_fp64_gm(size_t smem);
+int occupancy_solve_mixed(size_t smem);
+int occupancy_solve_mixed_gm(size_t smem);
 int device_sm_count();
 // cbx_solve on device buffers with at most max_grid CTAs (0: no cap).
 int solve_device(cbx_network* net, const cbx_cell_params* phi, const double* x0, int C, double t0, double t_end,
