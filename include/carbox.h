@@ -162,6 +162,20 @@ int cbx_network_destroy(cbx_network* net);
 /* Sizes and symbolic-analysis figures of a network. */
 int cbx_network_info(const cbx_network* net, cbx_netinfo* out);
 
+/*
+ * The host compiler's symbolic analysis of a network (Sec. 4 names the sparse
+ * structure of the problem), for checks; host memory only, no device access.
+ *   perm   [S]    internal -> user species index: the fill-reducing order
+ *                 (minimum degree on the pattern of J + J^T); or NULL.
+ *   fill   [S*S]  fill[i*S + j] = 1 when entry (i, j), in internal order, of
+ *                 the symbolic L + U of I - cJ (static diagonal pivots) is
+ *                 structurally non-zero, else 0; or NULL.
+ *   kdense        pivots k >= *kdense are factored over full index ranges
+ *                 (the dense tail of the FP64 shared-memory LU); or NULL.
+ * Errors: CBX_E_ARG for a NULL network.
+ */
+int cbx_network_symbolic(const cbx_network* net, int* perm, unsigned char* fill, int* kdense);
+
 /* Default options: rtol 1e-4, atol 1e-20, max_steps 100000, CBX_FP64,
    max_refine 5, refine_tol 1e-10. */
 int cbx_default_options(cbx_options* out);

@@ -88,6 +88,7 @@ def _load():
                                          C.POINTER(P)]),
         "cbx_network_destroy": (C.c_int, [P]),
         "cbx_network_info": (C.c_int, [P, C.POINTER(cbx_netinfo)]),
+        "cbx_network_symbolic": (C.c_int, [P, P, P, C.POINTER(C.c_int)]),
         "cbx_solve": (C.c_int, [P, P, P, C.c_int, C.c_double, C.c_double, C.POINTER(cbx_options), P, P, P, P]),
         "cbx_solve_host": (C.c_int, [P, P, P, C.c_int, C.c_double, C.c_double, C.POINTER(cbx_options), P, P,
                                      P, P]),
@@ -172,6 +173,15 @@ class Network:
         inf = cbx_netinfo()
         check(lib.cbx_network_info(self.handle, C.byref(inf)), "cbx_network_info")
         return {f: getattr(inf, f) for f, _ in cbx_netinfo._fields_}
+
+    def symbolic(self):
+        """(perm [S], fill [S, S] bool, kdense): the host compiler's ordering and L + U pattern."""
+        perm = np.zeros(self.S, np.int32)
+        fill = np.zeros((self.S, self.S), np.uint8)
+        kd = C.c_int()
+        check(lib.cbx_network_symbolic(self.handle, perm.ctypes.data_as(C.c_void_p), fill.ctypes.data_as(C.c_void_p),
+                                       C.byref(kd)), "cbx_network_symbolic")
+        return perm, fill.astype(bool), kd.value
 
     def close(self):
         if self.handle:

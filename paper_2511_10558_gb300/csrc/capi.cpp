@@ -192,6 +192,24 @@ int cbx_network_info(const cbx_network* net, cbx_netinfo* out) {
   return CBX_OK;
 }
 
+int cbx_network_symbolic(const cbx_network* net, int* perm, unsigned char* fill, int* kdense) {
+  if (!net) return fail(CBX_E_ARG, "net is NULL");
+  const HostNet& h = net->host;
+  const int S = h.S;
+  if (perm)
+    for (int i = 0; i < S; ++i) perm[i] = h.perm[i];
+  if (kdense) *kdense = h.kdense;
+  if (fill) {
+    memset(fill, 0, (size_t)S * S);
+    for (int k = 0; k < S; ++k) {
+      fill[(size_t)k * S + k] = 1;
+      for (int e = h.piv_lptr[k]; e < h.piv_lptr[k + 1]; ++e) fill[(size_t)h.piv_l[e] * S + k] = 1;
+      for (int e = h.piv_uptr[k]; e < h.piv_uptr[k + 1]; ++e) fill[(size_t)k * S + h.piv_u[e]] = 1;
+    }
+  }
+  return CBX_OK;
+}
+
 }  // extern "C"
 
 static int solve_impl(cbx_network* net, const cbx_cell_params* phi, const double* x0, int C, double t0,

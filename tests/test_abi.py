@@ -45,24 +45,76 @@ def test_host_compiler_figures(lib):
     assert 0 < info["lu_flops"] <= info["lu_flops_dense"] * 1.0001 + 150 * 150
 
 
-def test_host_compiler_fill_matches_dense_elimination(lib):
-    # the library's symbolic LU of I - cJ (after its ordering) has the fill of a
-    # dense elimination of the same pattern in any order it might use: check the
-    # fill count against brute-force elimination over the library's own order
-    # is not possible from outside, so check order-independent bounds instead:
-    # nnz(LU) >= nnz(J + I) and flops consistent with nnz.
+def _jacobian_pattern(net):
+    # J(i, l) != 0 when l is a reactant of a reaction whose net stoichiometry
+    # changes species i, plus the diagonal of I - cJ (user order)
+    S = net.n_species
+    pat = np.eye(S, dtype=bool)
+    for j in range(net.n_reactions):
+        nu = {}
+        for a in net.reac[j]:
+            if a >= 0:
+                nu[a] = nu.get(a, 0) - 1
+        for p in net.prod[j]:
+            if p >= 0:
+                nu[p] = nu.get(p, 0) + 1
+        for l in (a for a in net.reac[j] if a >= 0):
+            for i, v in nu.items():
+                if v != 0:
+                    pat[i, l] = True
+    return pat
+
+
+def _eliminate(F):
+    """Plain boolean Gaussian elimination with diagonal pivots, in order."""
+    F = F.copy()
+    S = F.shape[0]
+    flops = 0.0
+    for k in range(S):
+        rows = np.flatnonzero(F[k + 1:, k]) + k + 1
+        cols = np.flatnonzero(F[k, k + 1:]) + k + 1
+        F[np.ix_(rows, cols)] = True
+        flops += len(rows) + 2.0 * len(rows) * len(cols)
+    return F, flops
+
+
+@pytest.mark.parametrize("S,R", [(32, 200), (150, 1500), (500, 6000)])
+def test_host_compiler_fill_matches_dense_elimination(lib, S, R):
+    # bit-exact: the library's L + U pattern in its own order equals a plain
+    # boolean elimination of pattern(J + I) permuted to that order, and its
+    # flop count and nnz follow from that pattern
+    from paper_2511_10558_gb300 import synth
+    net = synth.make_network(S, R)
+    N = lib.Network.from_synth(net)
+    info = N.info()
+    perm, fill, kdense = N.symbolic()
+    assert sorted(perm) == list(range(S))
+    pat = _jacobian_pattern(net)
+    assert info["nnz_jac"] == pat.sum()
+    want, flops = _eliminate(pat[np.ix_(perm, perm)])
+    np.testing.assert_array_equal(fill, want)
+    assert info["nnz_lu"] == want.sum()
+    assert info["lu_flops"] == flops
+    assert 0 <= kdense <= S
+
+
+def test_host_compiler_order_is_minimum_degree(lib):
+    # property of the order: each eliminated node had the smallest degree (ties:
+    # smallest index) in the elimination graph of pattern(J + J^T) at its turn
     from paper_2511_10558_gb300 import synth
     net = synth.make_network(32, 200)
     N = lib.Network.from_synth(net)
-    info = N.info()
-    pat = np.eye(32, dtype=bool)
-    for j in range(net.n_reactions):
-        rc = [a for a in net.reac[j] if a >= 0]
-        parts = set(rc) | {p for p in net.prod[j] if p >= 0}
-        for l in rc:
-            for i in parts:
-                pat[i, l] = True
-    assert info["nnz_jac"] == pat.sum()
+    perm, _, _ = N.symbolic()
+    pat = _jacobian_pattern(net)
+    adj = (pat | pat.T) & ~np.eye(net.n_species, dtype=bool)
+    alive = np.ones(net.n_species, bool)
+    for v in perm:
+        deg = np.where(alive, (adj & alive[None, :]).sum(axis=1), np.iinfo(np.int64).max)
+        assert deg[v] == deg.min() and v == int(np.flatnonzero(deg == deg.min())[0])
+        nb = np.flatnonzero(adj[v] & alive)
+        alive[v] = False
+        adj[np.ix_(nb, nb)] = True
+        adj[nb, nb] = False
 
 
 def test_create_rejects_bad_input(lib):
