@@ -66,6 +66,10 @@ extern "C" {
 #define CBX_TWO_BODY 0    /* A + B -> products, k = alpha (T/300)^beta exp(-gamma/T) */
 #define CBX_COSMIC_RAY 1  /* X -> products,     k = alpha zeta                       */
 #define CBX_PHOTO 2       /* X -> products,     k = alpha G0 exp(-gamma A_V)         */
+#define CBX_CR_PHOTO 3    /* X -> products by secondary photons induced by cosmic
+                             rays (App. B.1), k = alpha (T/300)^beta gamma/(1 - omega) zeta:
+                             gamma holds the reaction's cosmic-ray efficiency E and
+                             omega is the network's grain albedo (cbx_network_set_albedo) */
 
 /* precision of the Newton linear algebra */
 #define CBX_FP64 0   /* LU, triangular solves and everything else in FP64 */
@@ -79,7 +83,7 @@ typedef struct {
 } cbx_species;
 
 typedef struct {
-  int type;     /* CBX_TWO_BODY, CBX_COSMIC_RAY or CBX_PHOTO */
+  int type;     /* CBX_TWO_BODY, CBX_COSMIC_RAY, CBX_PHOTO or CBX_CR_PHOTO */
   int reac[2];  /* reactant species indices; reac[1] = -1 for one-reactant types;
                    reac[0] == reac[1] is A + A (rate kappa x_A^2, A consumed twice) */
   int prod[4];  /* product species indices, -1 = absent; at least one product */
@@ -235,6 +239,15 @@ int cbx_solve_host(cbx_network* net, const cbx_cell_params* phi, const double* x
 int cbx_network_set_alpha(cbx_network* net, const double* alpha);
 
 /*
+ * Set the dust grain albedo omega (0 <= omega < 1) of the cosmic-ray-induced
+ * photo form (App. B.1: k = alpha (T/300)^beta E/(1 - omega) zeta) for every
+ * CBX_CR_PHOTO reaction of the network. A new network has omega = 0. Applies
+ * to solves issued after the call. Errors: CBX_E_ARG for a NULL network or
+ * omega outside [0, 1).
+ */
+int cbx_network_set_albedo(cbx_network* net, double omega);
+
+/*
  * Trajectory tape for the adjoint (Sec. 3: gradients of model outputs with
  * respect to chemical and physical inputs; the paper obtains them by automatic
  * differentiation of its solver, here a hand-written discrete adjoint of the
@@ -336,14 +349,23 @@ int cbx_server_destroy(cbx_server* server);
  * is a fixed 16 MiB array compiled into the library, which every GPU that
  * loads the library holds until the process exits.
  *
- * - Set-up: the first call made with a given device current looks up the
- *   array's device address (cudaGetSymbolAddress) and caches it; make that
- *   first call before any stream capture.
+ * - Set-up: the first call made in a CUDA context (with its device current)
+ *   looks up the array's device address (cudaGetSymbolAddress) and caches it
+ *   with the context's id; a new context (after cudaDeviceReset, say) gets a
+ *   new lookup. Make the first call of each context before any stream capture.
  * - The network's tables must already be on the current device (they are
  *   uploaded by cbx_network_create when a GPU is present); otherwise CBX_E_ARG.
- * - Limit: a network whose per-CTA scratch (8 * (3 R + nnz(J)) bytes, rounded
- *   up) exceeds the array is rejected with CBX_E_TOO_LARGE. When fewer CTAs
- *   fit than the device can run, fewer are launched (slower, same results).
+ * - Limit: each CTA needs 8 * (3 R + nnz(J)) bytes of scratch (rounded up to
+ *   256 B), plus, for networks whose Newton matrix does not fit in shared
+ *   memory (S > 256, e.g. 500 species), the matrix itself:
+ *   S * (S | 1) * 8 bytes (CBX_FP64) or * 4 bytes (CBX_MIXED). The number of
+ *   CTAs launched is min(C, CTAs the device can run, CTAs that fit in the
+ *   16 MiB); for the 500-species / 6000-reaction network that is 7 CTAs
+ *   (FP64) or 12 (CBX_MIXED) instead of one per SM, about 20x slower than
+ *   cbx_solve, with the same results. Networks the solver cannot run at all
+ *   are rejected with CBX_E_TOO_LARGE (within the solver's own limits, S <= 512
+ *   and R bounded by shared memory, a CTA needs at most about 5 MB, so every
+ *   network that the solver can run fits at least 3 CTAs).
  * - All calls share the one array and it keeps the last call's contents; the
  *   counter is cleared on `stream` at every call (cudaMemsetAsync). Calls
  *   whose kernels overlap on the GPU (other streams, other host threads) race

@@ -19,7 +19,8 @@ Reverse sweep for a cotangent Lam' on the difference array:
     dL/dp += c (nu^T mu)_j r_j(y) dlnk_j/dp   (per reaction j)
 rescale reverses with T^T; init adds h0 (nu^T Lam[1])_j r_j(y0) dlnk_j/dp.
 Parameters: ln alpha_j (dlnk_j = 1), ln n_H (two-body reactions, dlnk = 1) and
-T (two-body, dlnk/dT = beta_j/T + gamma_j/T^2).
+T (two-body, dlnk/dT = beta_j/T + gamma_j/T^2; cosmic-ray-induced photo,
+dlnk/dT = beta_j/T).
 """
 from __future__ import annotations
 
@@ -30,9 +31,13 @@ from . import bdf, chem
 
 
 def _log_k_derivatives(net, phi):
+    """(d ln k_j / d ln n_H, d ln k_j / dT): two-body coefficients carry n_H
+    (x = n / n_H) and (T/300)^beta exp(-gamma/T); the cosmic-ray-induced photo
+    form carries (T/300)^beta."""
     T = float(phi[1])
     tb = (net.rtype == chem.TWO_BODY).astype(float)
-    return tb, tb * (net.beta / T + net.gamma / T ** 2)
+    crp = (net.rtype == chem.CR_PHOTO).astype(float)
+    return tb, tb * (net.beta / T + net.gamma / T ** 2) + crp * net.beta / T
 
 
 def adjoint(net, phi, x0, program, cot_x):
@@ -83,12 +88,14 @@ def adjoint(net, phi, x0, program, cot_x):
 def environment_gradients(net, g_lnk):
     """(dL/d ln zeta, dL/d ln G0, dL/dA_V) of one cell from its per-reaction
     gradients dL/d ln k_j, which equal dL/d ln alpha_j because k_j is
-    proportional to alpha_j. Cosmic-ray coefficients are alpha_j zeta (Sec. 2);
-    photo coefficients alpha_j G0 exp(-gamma_j A_V) (App. B.1): so d ln k_j /
-    d ln zeta = 1 (cosmic ray), d ln k_j / d ln G0 = 1 and d ln k_j / dA_V =
-    -gamma_j (photo), and zero otherwise."""
+    proportional to alpha_j. Cosmic-ray coefficients are alpha_j zeta (Sec. 2),
+    and so are those of secondary photons induced by cosmic rays (App. B.1,
+    times (T/300)^beta E / (1 - omega)); photo coefficients are
+    alpha_j G0 exp(-gamma_j A_V) (App. B.1): so d ln k_j / d ln zeta = 1 (both
+    cosmic-ray forms), d ln k_j / d ln G0 = 1 and d ln k_j / dA_V = -gamma_j
+    (photo), and zero otherwise."""
     g = np.asarray(g_lnk, dtype=float)
-    cr = net.rtype == chem.COSMIC_RAY
+    cr = (net.rtype == chem.COSMIC_RAY) | (net.rtype == chem.CR_PHOTO)
     ph = net.rtype == chem.PHOTO
     return float(g[cr].sum()), float(g[ph].sum()), float(-(net.gamma[ph] * g[ph]).sum())
 

@@ -17,7 +17,7 @@ from __future__ import annotations
 
 import numpy as np
 
-TWO_BODY, COSMIC_RAY, PHOTO = 0, 1, 2
+TWO_BODY, COSMIC_RAY, PHOTO, CR_PHOTO = 0, 1, 2, 3
 
 
 def rate_coefficients(net, phi):
@@ -27,8 +27,13 @@ def rate_coefficients(net, phi):
     Cosmic-ray ionisation, Sec. 2:       k = alpha zeta
     Photo-reaction, App. B.1:            k = alpha F_UV exp(-gamma A_V)
     (the extinction factor written "k" in App. B.1 is the reaction's gamma; F_UV is G0).
+    Secondary photons induced by cosmic rays, App. B.1:
+                                         k = alpha (T/300)^beta E / (1 - omega) zeta
+    (E, the cosmic-ray efficiency of the reaction, is its gamma; omega is the
+    dust grain albedo of the network, ``net.albedo``).
     """
     n_H, T, A_V, G0, zeta = (float(v) for v in phi)
+    omega = float(getattr(net, "albedo", 0.0))
     k = np.zeros(net.n_reactions)
     for j in range(net.n_reactions):
         a, b, g = net.alpha[j], net.beta[j], net.gamma[j]
@@ -38,6 +43,8 @@ def rate_coefficients(net, phi):
             k[j] = a * zeta
         elif net.rtype[j] == PHOTO:
             k[j] = a * G0 * np.exp(-g * A_V)
+        elif net.rtype[j] == CR_PHOTO:
+            k[j] = a * (T / 300.0) ** b * g / (1.0 - omega) * zeta
         else:
             raise ValueError(f"unknown reaction type {net.rtype[j]}")
     return k

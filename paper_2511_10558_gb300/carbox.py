@@ -18,7 +18,7 @@ CBX_OK = 0
 CBX_E_ARG, CBX_E_CUDA, CBX_E_NOMEM, CBX_E_TOO_LARGE = -1, -2, -3, -4
 CBX_CELL_OK, CBX_CELL_MAX_STEPS, CBX_CELL_H_UNDERFLOW, CBX_CELL_BAD_INPUT = 0, 1, 2, 5
 CBX_CELL_TAPE_FULL = 6
-CBX_TWO_BODY, CBX_COSMIC_RAY, CBX_PHOTO = 0, 1, 2
+CBX_TWO_BODY, CBX_COSMIC_RAY, CBX_PHOTO, CBX_CR_PHOTO = 0, 1, 2, 3
 CBX_FP64, CBX_MIXED = 0, 1
 
 
@@ -93,6 +93,7 @@ def _load():
         "cbx_solve_host": (C.c_int, [P, P, P, C.c_int, C.c_double, C.c_double, C.POINTER(cbx_options), P, P,
                                      P, P]),
         "cbx_network_set_alpha": (C.c_int, [P, P]),
+        "cbx_network_set_albedo": (C.c_int, [P, C.c_double]),
         "cbx_tape_create": (C.c_int, [P, C.c_int, C.c_int, C.POINTER(P)]),
         "cbx_tape_destroy": (C.c_int, [P]),
         "cbx_solve_record": (C.c_int, [P, P, P, C.c_int, C.c_double, C.c_double, C.POINTER(cbx_options), P, P, P,
@@ -162,7 +163,12 @@ class Network:
 
     @classmethod
     def from_synth(cls, net):
-        return cls(net.composition, net.charge, net.rtype, net.reac, net.prod, net.alpha, net.beta, net.gamma)
+        n = cls(net.composition, net.charge, net.rtype, net.reac, net.prod, net.alpha, net.beta, net.gamma)
+        n.set_albedo(getattr(net, "albedo", 0.0))
+        return n
+
+    def set_albedo(self, omega):
+        check(lib.cbx_network_set_albedo(self.handle, float(omega)), "cbx_network_set_albedo")
 
     def set_alpha(self, alpha):
         a = np.ascontiguousarray(alpha, dtype=np.float64)

@@ -17,8 +17,9 @@ namespace {
 //                 dL/d ln alpha_j += c (nu^T mu)_j r_j(y)   (c = h/gamma_q)
 //   rescale:      Lam[1..q] <- T(rho)^T Lam[1..q]
 //   init (h0):    dL/d ln alpha_j += h0 (nu^T Lam[1])_j r_j(y0)
-// ln n_H and T enter through the two-body coefficients: d ln kappa_j / d ln n_H
-// = 1 and d ln kappa_j / dT = beta_j/T + gamma_j/T^2.
+// ln n_H enters through the two-body coefficients (d ln kappa_j / d ln n_H = 1)
+// and T through the two-body and cosmic-ray-induced photo forms:
+// d ln kappa_j / dT = beta_j/T + gamma_j/T^2 (two-body), beta_j/T (CR photo).
 
 // v <- U^{-T} v (U unit upper, so U^T is unit lower), blocks of 32.
 __device__ void forwardT_crout64(const double* M, int S, double* v) {
@@ -109,10 +110,8 @@ __device__ void grad_accumulate(const DevNet& n, const double* kap, const double
     if (b >= 0) r *= y[b];
     const double c = scale * w[j] * r;
     grow[j] += c;
-    if (n.rtype[j] == CBX_TWO_BODY) {
-      pn += c;
-      pt = fma(c, dlnk_dT[j], pt);
-    }
+    if (n.rtype[j] == CBX_TWO_BODY) pn += c;
+    pt = fma(c, dlnk_dT[j], pt);  // zero for the forms without T
   }
   *out_nH += block_sum(pn, red);
   *out_T += block_sum(pt, red);
@@ -145,9 +144,13 @@ __global__ void __launch_bounds__(NT, 1) grad_kernel(const GradArgs a) {
     const int nops = a.tape.nops[cell];
     if (a.status[cell] == CBX_CELL_OK && nops > 0) {
       const cbx_cell_params p = a.phi[cell];
-      rate_coefficients(n, p, kap);
-      for (int j = threadIdx.x; j < R; j += NT)
-        dT[j] = n.rtype[j] == CBX_TWO_BODY ? n.beta[j] / p.T + n.gamma[j] / (p.T * p.T) : 0.0;
+      rate_coefficients(n, a.alpha, p, kap);
+      // d ln k_j / dT: two-body (T/300)^beta exp(-gamma/T); CR-induced photo (T/300)^beta
+      for (int j = threadIdx.x; j < R; j += NT) {
+        const int t = n.rtype[j];
+        dT[j] = t == CBX_TWO_BODY ? n.beta[j] / p.T + n.gamma[j] / (p.T * p.T)
+                                  : (t == CBX_CR_PHOTO ? n.beta[j] / p.T : 0.0);
+      }
       for (int i = threadIdx.x; i < S; i += NT) {
         const int u = __ldg(n.perm + i);
         Lam[i] = a.cot[(size_t)u * a.C + cell];
@@ -254,9 +257,10 @@ __global__ void reduce_cells_kernel(const double* gcell, int C, int R, double* o
 
 // Environment gradients of each cell from its per-reaction gradients
 // dL/d ln k_j (k_j is proportional to alpha_j, so these are the per-cell
-// dL/d ln alpha_j): cosmic-ray coefficients carry the factor zeta (Sec. 2) and
-// photo coefficients G0 exp(-gamma_j A_V) (App. B.1), hence
-//   dL/d ln zeta = sum over cosmic-ray j,  dL/d ln G0 = sum over photo j,
+// dL/d ln alpha_j): cosmic-ray coefficients carry the factor zeta (Sec. 2), as
+// do those of secondary photons induced by cosmic rays (App. B.1), and photo
+// coefficients G0 exp(-gamma_j A_V) (App. B.1), hence
+//   dL/d ln zeta = sum over both cosmic-ray forms,  dL/d ln G0 = sum over photo j,
 //   dL/dA_V = -sum over photo j of gamma_j dL/d ln k_j.
 // One warp per cell: lanes take reactions lane, lane + 32, ..., and lane 0
 // ends with a fixed shuffle-tree sum (deterministic).
@@ -269,7 +273,7 @@ __global__ void env_grad_kernel(const double* gcell, int C, int R, const int* rt
   for (int j = lane; j < R; j += 32) {
     const int t = rtype[j];
     const double v = row[j];
-    if (t == CBX_COSMIC_RAY) {
+    if (t == CBX_COSMIC_RAY || t == CBX_CR_PHOTO) {
       z += v;
     } else if (t == CBX_PHOTO) {
       g += v;

@@ -62,7 +62,7 @@ int upload(cbx_network* n) {
          o_jcol = pk.add(h.jcol), o_jrp = pk.add(h.jrow_ptr), o_jgp = pk.add(h.jg_ptr),
          o_jgs = pk.add(h.jg_slot), o_jgl = pk.add(h.jg_len), o_jgt = pk.add(h.jg_term), o_plp = pk.add(h.piv_lptr), o_pl = pk.add(h.piv_l),
          o_pup = pk.add(h.piv_uptr), o_pu = pk.add(h.piv_u), o_perm = pk.add(h.perm),
-         o_rprod = pk.add(h.rprod);
+         o_rprod = pk.add(h.rprod), o_rj = pk.add(h.rj), o_gb = pk.add(h.gbeta), o_gg = pk.add(h.ggamma);
   cudaGetDevice(&n->device);
   cudaError_t e = cudaMalloc(&n->dbuf, pk.bytes.size());
   if (e != cudaSuccess) {
@@ -105,6 +105,11 @@ int upload(cbx_network* n) {
   d.piv_u = (const int*)(b + o_pu);
   d.perm = (const int*)(b + o_perm);
   d.rprod = (const int*)(b + o_rprod);
+  for (int t = 0; t <= kNumTypes; ++t) d.tptr[t] = h.tptr[t];
+  d.rj = (const int*)(b + o_rj);
+  d.gbeta = (const double*)(b + o_gb);
+  d.ggamma = (const double*)(b + o_gg);
+  d.albedo_factor = 1.0 / (1.0 - h.albedo);
   return CBX_OK;
 }
 
@@ -243,6 +248,7 @@ static int solve_impl(cbx_network* net, const cbx_cell_params* phi, const double
   cudaStream_t st = (cudaStream_t)stream;
   SolveArgs a{};
   a.net = net->dev;
+  a.alpha = net->dev.alpha;
   a.phi = phi;
   a.track = track;
   a.K = K;
@@ -355,6 +361,15 @@ int cbx_network_set_alpha(cbx_network* net, const double* alpha) {
   return CBX_OK;
 }
 
+int cbx_network_set_albedo(cbx_network* net, double omega) {
+  if (!net) return fail(CBX_E_ARG, "net is NULL");
+  if (!(omega >= 0.0 && omega < 1.0)) return fail(CBX_E_ARG, "omega must be in [0, 1)");
+  std::lock_guard<std::mutex> lock(net->mu);
+  net->host.albedo = omega;
+  net->dev.albedo_factor = 1.0 / (1.0 - omega);
+  return CBX_OK;
+}
+
 int cbx_tape_create(cbx_network* net, int C, int max_steps, cbx_tape** out) {
   if (!net || !out) return fail(CBX_E_ARG, "NULL argument");
   *out = nullptr;
@@ -431,6 +446,7 @@ int cbx_grad_env(cbx_tape* tape, const double* cot_x, void* stream, double* g_lo
   cudaStream_t st = (cudaStream_t)stream;
   GradArgs a{};
   a.net = net->dev;
+  a.alpha = net->dev.alpha;
   a.tape = tape->dev;
   a.phi = tape->phi;
   a.status = tape->status;

@@ -14,6 +14,7 @@ namespace cbx {
 constexpr int kMaxOrder = 5;           // BDF orders 1..5
 constexpr int kDiffRows = kMaxOrder + 3;  // difference array rows D[0..q+2]
 constexpr int kSegLen = 16;            // entries per right-hand-side gather segment
+constexpr int kNumTypes = 4;           // CBX_TWO_BODY .. CBX_CR_PHOTO
 
 // Device view of a compiled network: all species indices are internal
 // (fill-reducing order); perm maps internal -> user index.
@@ -44,6 +45,14 @@ struct DevNet {
   const int* piv_u;
   const int* perm;       // [S] internal -> user species index
   const int* rprod;      // [4R] products of each reaction (internal), -1 absent
+  // Reactions grouped by rate type, so that each type's rate coefficients are
+  // evaluated in a loop of its own: group t is positions tptr[t]..tptr[t+1]-1;
+  // position e holds reaction rj[e] with its beta and gamma in gbeta[e], ggamma[e].
+  int tptr[kNumTypes + 1];
+  const int* rj;         // [R]
+  const double* gbeta;   // [R]
+  const double* ggamma;  // [R]
+  double albedo_factor;  // 1 / (1 - omega) of the cosmic-ray-induced photo form
 };
 
 // Forward trajectory recorded for the adjoint: per cell the program of
@@ -71,6 +80,10 @@ struct HostNet {
   int njg = 0;
   std::vector<int> jg_ptr, jg_slot, jg_len, jg_term;
   std::vector<int> piv_lptr, piv_l, piv_uptr, piv_u;
+  int tptr[kNumTypes + 1] = {};
+  std::vector<int> rj;
+  std::vector<double> gbeta, ggamma;
+  double albedo = 0.0;  // omega
 };
 
 // Returns "" on success, else an error message.
@@ -81,6 +94,7 @@ std::vector<int> minimum_degree_order(const std::vector<uint8_t>& sym, int S);
 
 struct SolveArgs {
   DevNet net;
+  const double* alpha;  // [R] device: the alpha values of this solve (the network's, or a per-call set)
   const cbx_cell_params* phi;
   const double* x0;
   int C;
@@ -102,6 +116,7 @@ struct SolveArgs {
 
 struct GradArgs {
   DevNet net;
+  const double* alpha;  // [R] device: the alpha values of the recorded solve
   TapeDev tape;
   const cbx_cell_params* phi;  // [C] as recorded
   const int* status;           // [C] forward status

@@ -64,7 +64,7 @@ std::string compile_network(const cbx_species* sp, int S, const cbx_reaction* rx
   if (R > 0 && !rx) return "reactions is NULL";
   for (int j = 0; j < R; ++j) {
     const cbx_reaction& r = rx[j];
-    if (r.type != CBX_TWO_BODY && r.type != CBX_COSMIC_RAY && r.type != CBX_PHOTO) {
+    if (r.type != CBX_TWO_BODY && r.type != CBX_COSMIC_RAY && r.type != CBX_PHOTO && r.type != CBX_CR_PHOTO) {
       snprintf(msg, sizeof msg, "reaction %d: unknown type %d", j, r.type);
       return msg;
     }
@@ -137,6 +137,17 @@ std::string compile_network(const cbx_species* sp, int S, const cbx_reaction* rx
     n.beta[j] = rx[j].beta;
     n.gamma[j] = rx[j].gamma;
   }
+  // reactions grouped by rate type (stable within a type)
+  for (int t = 0; t < kNumTypes; ++t) {
+    n.tptr[t] = (int)n.rj.size();
+    for (int j = 0; j < R; ++j)
+      if (n.rtype[j] == t) {
+        n.rj.push_back(j);
+        n.gbeta.push_back(n.beta[j]);
+        n.ggamma.push_back(n.gamma[j]);
+      }
+  }
+  n.tptr[kNumTypes] = (int)n.rj.size();
   // right-hand side gather lists, segmented
   n.spec_seg.push_back(0);
   n.seg_ptr.push_back(0);

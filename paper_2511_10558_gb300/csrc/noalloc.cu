@@ -13,8 +13,12 @@
 // The array below is a file-scope __device__ array: every GPU that loads this
 // library holds kScratchBytes of it until the process exits, whether or not
 // this entry point is ever called. In host code its name is only a host-side
-// stand-in; the device address is obtained with cudaGetSymbolAddress once per
-// device (on the first call made with that device current) and cached.
+// stand-in; the device address is obtained with cudaGetSymbolAddress on the
+// first call made in a given CUDA context (with its device current) and
+// cached with that context's unique id, so that a context that is destroyed
+// and created again (cudaDeviceReset, a released primary context) gets the
+// address looked up again instead of a stale one.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,9 +38,42 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-void* g_scratch[kMaxDevices] = {};
+struct ScratchAddr {
+  unsigned long long ctx_id = 0;  // 0: not cached
+  void* ptr = nullptr;
+};
+ScratchAddr g_scratch[kMaxDevices];
 
 int fail(int code, const std::string& msg) { return cbx::record_error(code, msg); }
+
+// Unique id of the calling thread's current CUDA context, 0 when there is none
+// or the driver cannot tell (then the address is looked up on every call).
+// The driver functions are fetched through the runtime, so the library does not
+// link the driver library itself.
+unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = (GetCurrent)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (GetId)f;
+    cudaGetLastError();
+  });
+  if (!get_current || !get_id) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 }  // namespace
 
@@ -65,14 +102,17 @@ extern "C" int cbx_solve_noalloc(cbx_network* net, const cbx_cell_params* phi, c
   void* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch[dev]) {
-      e = cudaGetSymbolAddress(&g_scratch[dev], g_noalloc_scratch);
+    const unsigned long long id = current_context_id();
+    if (id != 0 && g_scratch[dev].ctx_id == id) {
+      scratch = g_scratch[dev].ptr;
+    } else {
+      e = cudaGetSymbolAddress(&scratch, g_noalloc_scratch);
       if (e != cudaSuccess) {
-        g_scratch[dev] = nullptr;
+        g_scratch[dev] = ScratchAddr{};
         return fail(CBX_E_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
       }
+      g_scratch[dev] = ScratchAddr{current_context_id(), scratch};
     }
-    scratch = g_scratch[dev];
   }
   const HostNet& h = net->host;
   const bool mixed = o.precision == CBX_MIXED;
@@ -90,6 +130,7 @@ extern "C" int cbx_solve_noalloc(cbx_network* net, const cbx_cell_params* phi, c
   const int grid = (int)std::min<long long>(std::min<long long>(C, (long long)occ * device_sm_count()), fit);
   SolveArgs a{};
   a.net = net->dev;
+  a.alpha = net->dev.alpha;
   a.phi = phi;
   a.x0 = x0;
   a.C = C;

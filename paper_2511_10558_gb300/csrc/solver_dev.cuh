@@ -107,20 +107,32 @@ __device__ __forceinline__ double growth(double err, int p, double* slot) {
 // ---------------------------------------------------------------- chemistry
 
 // kappa_j of one cell (Sec. 2 two-body and cosmic-ray forms, App. B.1 photo
-// form); two-body values carry the n_H factor of x = n / n_H.
-__device__ void rate_coefficients(const DevNet& n, const cbx_cell_params& p, double* kap) {
+// and cosmic-ray-induced photo forms); two-body values carry the n_H factor
+// of x = n / n_H. The reactions of each type form one contiguous group of the
+// network's grouped tables (Sec. 4: rates of identical mechanisms are
+// evaluated together), so every loop below is free of divergent branches.
+// alpha: [R], the alpha values of this solve.
+__device__ void rate_coefficients(const DevNet& n, const double* __restrict__ alpha, const cbx_cell_params& p,
+                                  double* kap) {
   const double lnT = log(p.T / 300.0);
   const double invT = 1.0 / p.T;
-  for (int j = threadIdx.x; j < n.R; j += NT) {
-    const int t = n.rtype[j];
-    double k;
-    if (t == CBX_TWO_BODY)
-      k = n.alpha[j] * exp(n.beta[j] * lnT - n.gamma[j] * invT) * p.n_H;
-    else if (t == CBX_COSMIC_RAY)
-      k = n.alpha[j] * p.zeta;
-    else
-      k = n.alpha[j] * p.G0 * exp(-n.gamma[j] * p.A_V);
-    kap[j] = k;
+  for (int e = n.tptr[CBX_TWO_BODY] + threadIdx.x; e < n.tptr[CBX_TWO_BODY + 1]; e += NT) {
+    const int j = __ldg(n.rj + e);
+    kap[j] = alpha[j] * exp(__ldg(n.gbeta + e) * lnT - __ldg(n.ggamma + e) * invT) * p.n_H;
+  }
+  for (int e = n.tptr[CBX_COSMIC_RAY] + threadIdx.x; e < n.tptr[CBX_COSMIC_RAY + 1]; e += NT) {
+    const int j = __ldg(n.rj + e);
+    kap[j] = alpha[j] * p.zeta;
+  }
+  for (int e = n.tptr[CBX_PHOTO] + threadIdx.x; e < n.tptr[CBX_PHOTO + 1]; e += NT) {
+    const int j = __ldg(n.rj + e);
+    kap[j] = alpha[j] * p.G0 * exp(-__ldg(n.ggamma + e) * p.A_V);
+  }
+  // k = alpha (T/300)^beta E / (1 - omega) zeta, E in the gamma field
+  const double crp = p.zeta * n.albedo_factor;
+  for (int e = n.tptr[CBX_CR_PHOTO] + threadIdx.x; e < n.tptr[CBX_CR_PHOTO + 1]; e += NT) {
+    const int j = __ldg(n.rj + e);
+    kap[j] = alpha[j] * exp(__ldg(n.gbeta + e) * lnT) * __ldg(n.ggamma + e) * crp;
   }
 }
 
@@ -1192,13 +1204,13 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
     __syncthreads();
     for (int i = threadIdx.x; i < S; i += NT) a.x_out[(size_t)__ldg(n.perm + i) * a.C + cell] = s.y[i];
   } else {
-    rate_coefficients(n, p, c.kap);
+    rate_coefficients(n, a.alpha, p, c.kap);
     __syncthreads();
     // with a track, the coefficients follow phi(t) to every time f or J is evaluated at
     double t_rates = a.t0;
     auto rates_at = [&](double tt) {
       if (a.track && tt != t_rates) {
-        rate_coefficients(n, track_params(a, cell, tt), c.kap);
+        rate_coefficients(n, a.alpha, track_params(a, cell, tt), c.kap);
         __syncthreads();
         t_rates = tt;
       }

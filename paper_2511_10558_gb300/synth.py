@@ -29,6 +29,8 @@ Recipe (all draws from ``numpy.random.Generator(PCG64(seed))``):
   beta U[-1, 1], gamma = 0 with probability 0.5 else U[0, 500] K.
   Cosmic-ray: alpha U[1, 1e3]. Photo: alpha log-uniform [1e-11, 1e-9] s^-1,
   gamma U[1, 3]. beta = gamma = 0 where unused.
+* Optional (``cr_photo_frac``): a share of the cosmic-ray reactions becomes
+  the cosmic-ray-induced photo form of App. B.1 (see make_network).
 * Cells. One cell: n_H = 1e4 cm^-3, T = 20 K, A_V = 5, G0 = 1,
   zeta = 1.3e-17 s^-1 (the galactic value zeta_0 of Sec. 4). Batches:
   n_H log-uniform [1e2, 1e6], T U[10, 300] K, A_V U[0, 20], G0 = 1,
@@ -45,6 +47,7 @@ import numpy as np
 TWO_BODY = 0
 COSMIC_RAY = 1
 PHOTO = 2
+CR_PHOTO = 3   # secondary photons induced by cosmic rays (App. B.1)
 
 ELEMENTS = ("H", "He", "C", "N", "O")
 ZETA0 = 1.3e-17          # s^-1, galactic cosmic-ray ionisation rate (Sec. 4)
@@ -85,6 +88,7 @@ class Network:
     alpha: np.ndarray
     beta: np.ndarray
     gamma: np.ndarray
+    albedo: float = 0.0   # dust grain albedo omega of the CR-photo form (App. B.1)
 
     @property
     def n_species(self) -> int:
@@ -115,8 +119,31 @@ def _sub_keys(a, b):
     return tuple(x - y for x, y in zip(a, b))
 
 
-def make_network(n_species: int, n_reactions: int, seed: int | None = None) -> Network:
-    """Draw a balanced synthetic network of the given size (seed default 1000 + S)."""
+def make_network(n_species: int, n_reactions: int, seed: int | None = None,
+                 cr_photo_frac: float = 0.0) -> Network:
+    """Draw a balanced synthetic network of the given size (seed default 1000 + S).
+
+    cr_photo_frac > 0 turns that fraction of the cosmic-ray reactions into
+    reactions by secondary photons induced by cosmic rays (App. B.1), drawn
+    from a separate stream so that the rest of the network is unchanged:
+    alpha U[0.5, 2], beta = 0 with probability 0.5 else U[0, 1], efficiency
+    E (the gamma field) U[100, 5000], and a grain albedo omega = 0.5.
+    """
+    net = _draw_network(n_species, n_reactions, seed)
+    if cr_photo_frac > 0.0:
+        rng = np.random.default_rng((1000 + n_species if seed is None else seed) + 77)
+        cr = np.flatnonzero(net.rtype == COSMIC_RAY)
+        pick = np.sort(rng.choice(cr, size=int(round(cr_photo_frac * len(cr))), replace=False))
+        for j in pick:
+            net.rtype[j] = CR_PHOTO
+            net.alpha[j] = rng.uniform(0.5, 2.0)
+            net.beta[j] = 0.0 if rng.random() < 0.5 else rng.uniform(0.0, 1.0)
+            net.gamma[j] = rng.uniform(100.0, 5000.0)
+        net.albedo = 0.5
+    return net
+
+
+def _draw_network(n_species: int, n_reactions: int, seed: int | None) -> Network:
     if seed is None:
         seed = 1000 + n_species
     if n_species < len(_FIXED):

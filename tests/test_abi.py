@@ -132,3 +132,13 @@ def test_create_rejects_bad_input(lib):
     assert lib.lib.cbx_network_create(sp, 2, rx, 1, C.byref(h)) == lib.CBX_E_ARG
     rx[0].type = 9
     assert lib.lib.cbx_network_create(sp, 2, rx, 1, C.byref(h)) == lib.CBX_E_ARG
+
+
+def test_set_albedo_checks(lib):
+    import ctypes as C
+    from paper_2511_10558_gb300 import synth
+    N = lib.Network.from_synth(synth.make_network(32, 200, cr_photo_frac=0.5))
+    assert lib.lib.cbx_network_set_albedo(N.handle, C.c_double(0.3)) == lib.CBX_OK
+    for bad in (1.0, -0.1, float("nan"), 2.0):
+        assert lib.lib.cbx_network_set_albedo(N.handle, C.c_double(bad)) == lib.CBX_E_ARG
+    assert lib.lib.cbx_network_set_albedo(None, C.c_double(0.3)) == lib.CBX_E_ARG

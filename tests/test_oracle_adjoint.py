@@ -55,6 +55,30 @@ def test_photo_decay_environment_sensitivity():
     assert g_av == pytest.approx(-gam * exact, rel=1e-6)
 
 
+def test_cr_photo_decay_sensitivity():
+    # A -> B by secondary photons induced by cosmic rays (App. B.1),
+    # k = alpha (T/300)^beta E/(1 - omega) zeta: x_B = a (1 - exp(-k t)), so
+    # d x_B / d ln k = a k t exp(-k t) = d x_B / d ln zeta, d x_B / dT = (beta/T) that,
+    # and no n_H, G0 or A_V dependence
+    beta, T = 0.7, 40.0
+    net = tiny(2, [(synth.CR_PHOTO, (0,), (1,), 1.3, beta, 3000.0)])
+    net.albedo = 0.5
+    phi = [1e4, T, 2.0, 1.0, 1.3e-17]
+    k = chem.rate_coefficients(net, phi)[0]
+    assert k == pytest.approx(1.3 * (T / 300) ** beta * 3000 / 0.5 * 1.3e-17, rel=1e-14)
+    t = 2.0 / k
+    a = 1e-3
+    res = bdf.solve_cell(net, phi, np.array([a, 1e-20]), 0.0, t, 1e-10, 1e-30, record=True)
+    g_la, g_nH, g_T = adj.adjoint(net, phi, [a, 1e-20], res.program, np.array([0.0, 1.0]))
+    exact = a * k * t * np.exp(-k * t)
+    assert g_la[0] == pytest.approx(exact, rel=1e-6)
+    assert g_nH == 0.0
+    assert g_T == pytest.approx(beta / T * exact, rel=1e-6)
+    g_z, g_g0, g_av = adj.environment_gradients(net, g_la)
+    assert g_z == pytest.approx(exact, rel=1e-6)
+    assert g_g0 == 0.0 and g_av == 0.0
+
+
 def test_second_order_sensitivity():
     net = tiny(3, [(synth.TWO_BODY, (0, 1), (2,), 1e-10, 0.5, 20.0)])
     phi = [1e3, 50.0, 0.0, 1.0, 0.0]

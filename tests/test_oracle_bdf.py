@@ -62,10 +62,12 @@ def _solve(net, phi, x0, t_end, rtol=1e-10, atol=1e-30):
     return res.x
 
 
-@pytest.mark.parametrize("rt", [synth.COSMIC_RAY, synth.PHOTO])
+@pytest.mark.parametrize("rt", [synth.COSMIC_RAY, synth.PHOTO, synth.CR_PHOTO])
 def test_first_order_decay(rt):
     # A -> B: x_A = a exp(-k t), x_B = b0 + a (1 - exp(-k t))
-    net = tiny(2, [(rt, (0,), (1,), 50.0 if rt == synth.COSMIC_RAY else 1e-10, 0, 1.5)])
+    alpha = {synth.COSMIC_RAY: 50.0, synth.PHOTO: 1e-10, synth.CR_PHOTO: 1.2}[rt]
+    net = tiny(2, [(rt, (0,), (1,), alpha, 0.4 if rt == synth.CR_PHOTO else 0, 1500.0 if rt == synth.CR_PHOTO else 1.5)])
+    net.albedo = 0.5
     phi = [1e4, 20.0, 0.5, 1.0, 1.3e-17]
     k = chem.rate_coefficients(net, phi)[0]
     t = 4.0 / k

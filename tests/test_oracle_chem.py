@@ -20,13 +20,16 @@ decimal.getcontext().prec = 40
 D = decimal.Decimal
 
 
-def _rate_decimal(rt, a, b, g, phi):
+def _rate_decimal(rt, a, b, g, phi, omega=0.0):
     n_H, T, A_V, G0, zeta = (D(repr(float(v))) for v in phi)
     a, b, g = D(repr(float(a))), D(repr(float(b))), D(repr(float(g)))
     if rt == synth.TWO_BODY:
         return a * ((b * (T / D(300)).ln()).exp()) * (-(g / T)).exp()
     if rt == synth.COSMIC_RAY:
         return a * zeta
+    if rt == synth.CR_PHOTO:
+        # App. B.1: alpha (T/300)^beta E / (1 - omega) zeta, E in the gamma field
+        return a * ((b * (T / D(300)).ln()).exp()) * g / (D(1) - D(repr(float(omega)))) * zeta
     return a * G0 * (-(g * A_V)).exp()
 
 
@@ -44,6 +47,35 @@ def test_rates_against_decimal(net150, seed):
     tb = net150.rtype == synth.TWO_BODY
     np.testing.assert_array_equal(kap[tb], k[tb] * phi[0])
     np.testing.assert_array_equal(kap[~tb], k[~tb])
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_cr_photo_rates_against_decimal(seed):
+    net = synth.make_network(150, 1500, cr_photo_frac=0.4)
+    assert (net.rtype == synth.CR_PHOTO).sum() > 50 and net.albedo == 0.5
+    phi = synth.cells(1, seed=seed)[0]
+    k = chem.rate_coefficients(net, phi)
+    for j in np.flatnonzero(net.rtype == synth.CR_PHOTO):
+        ref = _rate_decimal(synth.CR_PHOTO, net.alpha[j], net.beta[j], net.gamma[j], phi, net.albedo)
+        assert abs(D(repr(float(k[j]))) / ref - 1) < D("1e-14"), j
+    # one reactant: no n_H factor in the effective coefficient
+    kap = chem.effective_coefficients(net, phi)
+    crp = net.rtype == synth.CR_PHOTO
+    np.testing.assert_array_equal(kap[crp], k[crp])
+
+
+def test_cr_photo_special_values():
+    # T = 300 K: (T/300)^beta = 1, so k = alpha E / (1 - omega) zeta; omega = 0 gives alpha E zeta
+    net = tiny(2, [(synth.CR_PHOTO, (0,), (1,), 1.5, 0.8, 2000.0)])
+    net.albedo = 0.6
+    k = chem.rate_coefficients(net, [1e4, 300.0, 7.0, 3.0, 2e-17])[0]
+    assert k == pytest.approx(1.5 * 2000.0 / 0.4 * 2e-17, rel=1e-15)
+    net.albedo = 0.0
+    assert chem.rate_coefficients(net, [1e4, 300.0, 0.0, 0.0, 2e-17])[0] == pytest.approx(1.5 * 2000 * 2e-17,
+                                                                                         rel=1e-15)
+    # no dependence on A_V or G0; T enters as (T/300)^beta
+    k2 = chem.rate_coefficients(net, [1e2, 75.0, 0.0, 9.0, 2e-17])[0]
+    assert k2 == pytest.approx(1.5 * 0.25 ** 0.8 * 2000 * 2e-17, rel=1e-14)
 
 
 def test_rate_special_values():

@@ -76,3 +76,19 @@ def test_tracks_recipe():
     np.testing.assert_allclose(tr[:, -1, 2], 1.5 * phi[:, 1])            # T x1.5
     np.testing.assert_allclose(tr[:, -1, 3], phi[:, 2] + 5.0)            # A_V + 5 mag
     np.testing.assert_array_equal(tr[:, :, 4:], np.repeat(phi[:, None, 3:], 4, axis=1))
+
+
+def test_cr_photo_share_leaves_the_rest_unchanged():
+    base = synth.make_network(150, 1500)
+    net = synth.make_network(150, 1500, cr_photo_frac=0.3)
+    crp = net.rtype == synth.CR_PHOTO
+    assert crp.sum() == round(0.3 * (base.rtype == synth.COSMIC_RAY).sum())
+    assert np.all(base.rtype[crp] == synth.COSMIC_RAY)
+    np.testing.assert_array_equal(net.reac, base.reac)
+    np.testing.assert_array_equal(net.prod, base.prod)
+    for f in ("alpha", "beta", "gamma"):
+        np.testing.assert_array_equal(getattr(net, f)[~crp], getattr(base, f)[~crp])
+    assert np.all((net.alpha[crp] >= 0.5) & (net.alpha[crp] <= 2.0))
+    assert np.all((net.gamma[crp] >= 100) & (net.gamma[crp] <= 5000))
+    assert np.all((net.beta[crp] >= 0) & (net.beta[crp] <= 1))
+    assert net.albedo == 0.5 and base.albedo == 0.0
