@@ -258,7 +258,7 @@ int cbx_network_set_albedo(cbx_network* net, double omega);
  * initial abundances: the whole forward trajectory is checkpointed, one state
  * per accepted step, so the reverse sweep needs no recomputation.
  *   max_steps: accepted steps a cell may record (cells beyond it end with
- *   CBX_CELL_TAPE_FULL). Device memory: C * (max_steps * (8 S + 2 * 16) + ...).
+ *   CBX_CELL_TAPE_FULL). Device memory: C * (max_steps * (8 S + 8 + 4 * 12) + ...).
  * Library-owned; free with cbx_tape_destroy.
  */
 int cbx_tape_create(cbx_network* net, int C, int max_steps, cbx_tape** out);
@@ -267,11 +267,49 @@ int cbx_tape_destroy(cbx_tape* tape);
 /*
  * cbx_solve that also records the trajectory into `tape` (same arguments as
  * cbx_solve; C must not exceed the tape's capacity). The tape remembers phi,
- * x0, t0 and t_end for cbx_grad.
+ * x0, alpha, t0 and t_end for cbx_grad.
  */
 int cbx_solve_record(cbx_network* net, const cbx_cell_params* phi, const double* x0, int C, double t0,
                      double t_end, const cbx_options* opt, void* stream, double* x_out, int* cell_status,
                      cbx_cell_stats* stats, cbx_tape* tape);
+
+/*
+ * cbx_solve_track that also records the trajectory into `tape` (arguments as
+ * cbx_solve_track; C must not exceed the tape's capacity). The tape keeps a
+ * copy of the tracks and the time of every accepted step, so that cbx_grad
+ * re-evaluates the rate coefficients of phi(t) at each step as the forward
+ * solve did. Gradients through a track (cbx_grad / cbx_grad_env):
+ *   g_logalpha, g_lnzeta, g_lnG0: as for a constant environment;
+ *   g_lognH: derivative with respect to ln of a common factor on the n_H of
+ *            every knot of the cell's track;
+ *   g_T:     derivative with respect to a common shift (K) of the T of every
+ *            knot; g_AV likewise for a common shift of A_V (mag).
+ * Errors: those of cbx_solve_track and cbx_solve_record.
+ */
+int cbx_solve_track_record(cbx_network* net, const double* track, int K, const double* x0, int C, double t0,
+                           double t_end, const cbx_options* opt, void* stream, double* x_out, int* cell_status,
+                           cbx_cell_stats* stats, cbx_tape* tape);
+
+/*
+ * The time t_new (seconds) of every accepted step recorded for one cell, to
+ * the host (for checks); at most cap values. Returns the number of recorded
+ * steps (>= 0) or a negative error code. Synchronises the device.
+ */
+int cbx_tape_step_times(const cbx_tape* tape, int cell, double* t_new, int cap);
+
+/*
+ * cbx_solve (tape == NULL) or cbx_solve_record (tape given) with the network's
+ * alpha parameters replaced, for this call only, by alpha [R] (device pointer,
+ * reaction order of cbx_network_create). The network itself is not changed,
+ * so other users of it (other streams, a server, later calls) are not
+ * affected: this is how a differentiable solve in ln alpha (Sec. 3:
+ * sensitivity to rate coefficients) runs without touching shared state. A
+ * tape records the alpha it was solved with; cbx_grad uses that one.
+ * Errors: those of cbx_solve / cbx_solve_record, CBX_E_ARG for a NULL alpha.
+ */
+int cbx_solve_with_alpha(cbx_network* net, const double* alpha, const cbx_cell_params* phi, const double* x0, int C,
+                         double t0, double t_end, const cbx_options* opt, void* stream, double* x_out,
+                         int* cell_status, cbx_cell_stats* stats, cbx_tape* tape);
 
 /*
  * Discrete adjoint (FP64) of the recorded solve: for the cotangent
@@ -279,8 +317,10 @@ int cbx_solve_record(cbx_network* net, const cbx_cell_params* phi, const double*
  *   g_logalpha [R]  dL/d ln alpha_j summed over cells (device; deterministic order),
  *   g_lognH   [C]  dL/d ln n_H per cell (device),
  *   g_T       [C]  dL/dT per cell, T in K (device).
- * Step sizes and orders are those of the recorded forward solve; each
- * corrector is differentiated as if solved exactly. Cells whose status was
+ * Step sizes and orders are those of the recorded forward solve, and so are
+ * the alpha values (the network's at record time, or those passed to
+ * cbx_solve_with_alpha); each corrector is differentiated as if solved
+ * exactly. Cells whose status was
  * not CBX_CELL_OK get zero gradients. Any output pointer may be NULL.
  */
 int cbx_grad(cbx_tape* tape, const double* cot_x, void* stream, double* g_logalpha, double* g_lognH,

@@ -40,11 +40,25 @@ def _log_k_derivatives(net, phi):
     return tb, tb * (net.beta / T + net.gamma / T ** 2) + crp * net.beta / T
 
 
-def adjoint(net, phi, x0, program, cot_x):
-    """Gradients of <cot_x, x(t_end)> w.r.t. (ln alpha [R], ln n_H, T) for one cell."""
-    kappa = chem.effective_coefficients(net, phi)
+def _environment(phi, track, t):
+    """The cell's environment at time t: phi, or the track's phi(t)."""
+    return phi if track is None else bdf.track_params(track, t)
+
+
+def adjoint(net, phi, x0, program, cot_x, track=None, t0=0.0):
+    """Gradients of <cot_x, x(t_end)> w.r.t. (ln alpha [R], ln n_H, T) for one cell.
+
+    With a track (phi is then unused), every step's coefficients are those of
+    phi(t_new) and the initial difference's those of phi(t0), as in the
+    forward solve; ln n_H and T are then a common factor on the track's n_H
+    and a common shift of its T."""
     nu = chem.stoichiometry(net)
-    dlnH, dT = _log_k_derivatives(net, phi)
+
+    def coefficients(t):
+        p = _environment(phi, track, t)
+        return (chem.effective_coefficients(net, p),) + _log_k_derivatives(net, p)
+
+    kappa, dlnH, dT = coefficients(t0)
     S = len(x0)
     Lam = np.zeros((bdf.MAX_ORDER + 3, S))
     Lam[0] = cot_x
@@ -61,7 +75,9 @@ def adjoint(net, phi, x0, program, cot_x):
 
     for op in reversed(program):
         if op[0] == "step":
-            _, q, h, _t, y = op
+            _, q, h, t_new, y = op
+            if track is not None:
+                kappa, dlnH, dT = coefficients(t_new)
             c = h / bdf.GAMMA[q]
             lam_d = Lam[:q + 3].sum(axis=0)
             new = Lam.copy()
@@ -81,6 +97,8 @@ def adjoint(net, phi, x0, program, cot_x):
             _, q, rho = op
             Lam[1:q + 1] = bdf.rescale_matrix(q, rho).T @ Lam[1:q + 1]
         elif op[0] == "init":
+            if track is not None:
+                kappa, dlnH, dT = coefficients(t0)
             accumulate(op[1], nu.T @ Lam[1], np.asarray(x0, float))
     return g_la, g_nH, g_T
 
@@ -100,14 +118,16 @@ def environment_gradients(net, g_lnk):
     return float(g[cr].sum()), float(g[ph].sum()), float(-(net.gamma[ph] * g[ph]).sum())
 
 
-def replay(net, phi, x0, program, newton_tol=1e-13, max_iter=60):
+def replay(net, phi, x0, program, newton_tol=1e-13, max_iter=60, track=None, t0=0.0):
     """Re-run a recorded program with each corrector solved to convergence.
 
     Full Newton (fresh Jacobian every iteration) until the max-norm of the
     update relative to |y| + 1e-30 is below newton_tol. Returns x(t_end) and
-    the program with the replayed step results (for ``adjoint``).
+    the program with the replayed step results (for ``adjoint``). With a
+    track, each step uses the coefficients of phi(t_new) (its recorded time)
+    and the initial difference those of phi(t0).
     """
-    kappa = chem.effective_coefficients(net, phi)
+    kappa = chem.effective_coefficients(net, _environment(phi, track, t0))
     nu = chem.stoichiometry(net)
     y0 = np.asarray(x0, float)
     S = len(y0)
@@ -124,6 +144,8 @@ def replay(net, phi, x0, program, newton_tol=1e-13, max_iter=60):
             out.append(op)
         else:
             _, q, h, t_new, _y = op
+            if track is not None:
+                kappa = chem.effective_coefficients(net, bdf.track_params(track, t_new))
             c = h / bdf.GAMMA[q]
             y_p = D[:q + 1].sum(axis=0)
             psi = (bdf.GAMMA[1:q + 1] @ D[1:q + 1]) / bdf.GAMMA[q]

@@ -98,11 +98,16 @@ def _load():
         "cbx_tape_destroy": (C.c_int, [P]),
         "cbx_solve_record": (C.c_int, [P, P, P, C.c_int, C.c_double, C.c_double, C.POINTER(cbx_options), P, P, P,
                                        P, P]),
+        "cbx_solve_with_alpha": (C.c_int, [P, P, P, P, C.c_int, C.c_double, C.c_double, C.POINTER(cbx_options), P,
+                                           P, P, P, P]),
         "cbx_grad": (C.c_int, [P, P, P, P, P, P]),
         "cbx_grad_env": (C.c_int, [P, P, P, P, P, P, P, P, P]),
         "cbx_solve_track": (C.c_int, [P, P, C.c_int, P, C.c_int, C.c_double, C.c_double, C.POINTER(cbx_options), P,
                                       P, P, P]),
         "cbx_tape_program": (C.c_int, [P, C.c_int, P, P, P, C.c_int]),
+        "cbx_tape_step_times": (C.c_int, [P, C.c_int, P, C.c_int]),
+        "cbx_solve_track_record": (C.c_int, [P, P, C.c_int, P, C.c_int, C.c_double, C.c_double,
+                                             C.POINTER(cbx_options), P, P, P, P, P]),
         "cbx_server_create": (C.c_int, [C.c_size_t, C.c_int, C.c_int, C.POINTER(P)]),
         "cbx_server_submit": (C.c_int, [P, P, P, P, C.c_int, C.c_double, C.c_double, C.POINTER(cbx_options),
                                         C.POINTER(C.c_uint64)]),
@@ -296,6 +301,14 @@ class Tape:
             raise CarboxError(n, "cbx_tape_program")
         return [(int(kinds[i]), int(qs[i]), float(vals[i])) for i in range(min(n, cap))]
 
+    def step_times(self, cell, cap=100000):
+        """t_new of every recorded accepted step of one cell (numpy)."""
+        ts = np.zeros(cap)
+        n = lib.cbx_tape_step_times(self.handle, int(cell), ts.ctypes.data_as(C.c_void_p), cap)
+        if n < 0:
+            raise CarboxError(n, "cbx_tape_step_times")
+        return ts[:min(n, cap)].copy()
+
     def close(self):
         if self.handle:
             lib.cbx_tape_destroy(self.handle)
@@ -324,6 +337,46 @@ def solve_record(net, tape, phi, x0, t0, t_end, opt=None, stream=None, stats=Non
     check(lib.cbx_solve_record(net.handle, _ptr(phi), _ptr(x0), Cn, float(t0), float(t_end), C.byref(o),
                                C.c_void_p(stream.cuda_stream), _ptr(x_out), _ptr(status), _ptr(stats),
                                tape.handle), "cbx_solve_record")
+    return x_out, status
+
+
+def solve_with_alpha(net, alpha, phi, x0, t0, t_end, opt=None, stream=None, tape=None, stats=None):
+    """cbx_solve_with_alpha on torch CUDA tensors: the network's alpha replaced by
+    alpha [R] (f64, device) for this call only; records into ``tape`` when given.
+    Returns (x_out [S, C], status [C] int32)."""
+    import torch
+    Cn = phi.shape[0]
+    assert alpha.is_cuda and alpha.dtype == torch.float64 and alpha.is_contiguous() and tuple(alpha.shape) == (net.R,)
+    assert phi.is_cuda and phi.dtype == torch.float64 and phi.is_contiguous() and phi.shape[1] == 5
+    assert x0.is_cuda and x0.dtype == torch.float64 and x0.is_contiguous() and tuple(x0.shape) == (net.S, Cn)
+    if stats is not None:
+        assert stats.dtype == torch.int32 and stats.is_contiguous() and tuple(stats.shape) == (Cn, STATS_INTS)
+    x_out = torch.empty((net.S, Cn), dtype=torch.float64, device=phi.device)
+    status = torch.empty(Cn, dtype=torch.int32, device=phi.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(phi.device)
+    o = opt if opt is not None else options()
+    check(lib.cbx_solve_with_alpha(net.handle, _ptr(alpha), _ptr(phi), _ptr(x0), Cn, float(t0), float(t_end),
+                                   C.byref(o), C.c_void_p(stream.cuda_stream), _ptr(x_out), _ptr(status),
+                                   _ptr(stats), tape.handle if tape is not None else None), "cbx_solve_with_alpha")
+    return x_out, status
+
+
+def solve_track_record(net, tape, track, x0, t0, t_end, opt=None, stream=None, stats=None):
+    """cbx_solve_track_record on torch CUDA tensors: track [C, K, 6] f64, x0 [S, C];
+    returns (x_out [S, C], status [C] int32)."""
+    import torch
+    assert track.is_cuda and track.dtype == torch.float64 and track.is_contiguous() and track.dim() == 3
+    Cn, K = int(track.shape[0]), int(track.shape[1])
+    assert x0.is_cuda and x0.dtype == torch.float64 and x0.is_contiguous() and tuple(x0.shape) == (net.S, Cn)
+    x_out = torch.empty((net.S, Cn), dtype=torch.float64, device=track.device)
+    status = torch.empty(Cn, dtype=torch.int32, device=track.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(track.device)
+    o = opt if opt is not None else options()
+    check(lib.cbx_solve_track_record(net.handle, _ptr(track), K, _ptr(x0), Cn, float(t0), float(t_end), C.byref(o),
+                                     C.c_void_p(stream.cuda_stream), _ptr(x_out), _ptr(status), _ptr(stats),
+                                     tape.handle), "cbx_solve_track_record")
     return x_out, status
 
 
@@ -363,18 +416,19 @@ def _make_function():
     class CellSolve(torch.autograd.Function):
         """log10 x(t_end) [S, C] as a function of (ln alpha [R], ln n_H [C], T [C]).
 
-        Forward: cbx_network_set_alpha + cbx_solve_record (FP64 or mixed, per
-        ``opt``); backward: cbx_grad, the hand-written discrete adjoint.
-        Other inputs (x0, A_V, G0, zeta, times) are constants.
+        Forward: cbx_solve_with_alpha recording a tape (FP64 or mixed, per
+        ``opt``), with alpha = exp(ln alpha) for this call only (the network
+        is not modified); backward: cbx_grad, the hand-written discrete
+        adjoint. Other inputs (x0, A_V, G0, zeta, times) are constants.
         """
 
         @staticmethod
         def forward(ctx, log_alpha, log_nH, T, net, x0, av_g0_zeta, t_end, opt, max_steps):
-            net.set_alpha(torch.exp(log_alpha.detach()).cpu().numpy())
+            alpha = torch.exp(log_alpha.detach()).to(device=x0.device, dtype=torch.float64).contiguous()
             phi = torch.stack([torch.exp(log_nH.detach()), T.detach(), av_g0_zeta[:, 0], av_g0_zeta[:, 1],
                                av_g0_zeta[:, 2]], dim=1).contiguous()
             tape = Tape(net, phi.shape[0], max_steps)
-            x, status = solve_record(net, tape, phi, x0, 0.0, t_end, opt)
+            x, status = solve_with_alpha(net, alpha, phi, x0, 0.0, t_end, opt, tape=tape)
             ctx.tape, ctx.x, ctx.status = tape, x, status
             return torch.log10(x)
 

@@ -143,14 +143,20 @@ __global__ void __launch_bounds__(NT, 1) grad_kernel(const GradArgs a) {
     double gnH = 0.0, gT = 0.0;
     const int nops = a.tape.nops[cell];
     if (a.status[cell] == CBX_CELL_OK && nops > 0) {
-      const cbx_cell_params p = a.phi[cell];
-      rate_coefficients(n, a.alpha, p, kap);
-      // d ln k_j / dT: two-body (T/300)^beta exp(-gamma/T); CR-induced photo (T/300)^beta
-      for (int j = threadIdx.x; j < R; j += NT) {
-        const int t = n.rtype[j];
-        dT[j] = t == CBX_TWO_BODY ? n.beta[j] / p.T + n.gamma[j] / (p.T * p.T)
-                                  : (t == CBX_CR_PHOTO ? n.beta[j] / p.T : 0.0);
-      }
+      // rate coefficients and d ln k_j / dT of the environment p: two-body
+      // (T/300)^beta exp(-gamma/T); CR-induced photo (T/300)^beta
+      auto rates_for = [&](const cbx_cell_params& p) {
+        rate_coefficients(n, a.alpha, p, kap);
+        for (int j = threadIdx.x; j < R; j += NT) {
+          const int t = n.rtype[j];
+          dT[j] = t == CBX_TWO_BODY ? n.beta[j] / p.T + n.gamma[j] / (p.T * p.T)
+                                    : (t == CBX_CR_PHOTO ? n.beta[j] / p.T : 0.0);
+        }
+        __syncthreads();
+      };
+      // with a track, the step at t_new used the coefficients of phi(t_new),
+      // the initial difference D[1] = h0 f(y0) those of phi(t0)
+      if (!a.track) rates_for(a.phi[cell]);
       for (int i = threadIdx.x; i < S; i += NT) {
         const int u = __ldg(n.perm + i);
         Lam[i] = a.cot[(size_t)u * a.C + cell];
@@ -167,6 +173,7 @@ __global__ void __launch_bounds__(NT, 1) grad_kernel(const GradArgs a) {
         const double v = vv[o];
         if (kind == kOpStep) {
           --sidx;
+          if (a.track) rates_for(track_params(a.track, a.K, cell, a.tape.ts[(size_t)cell * a.tape.cap_steps + sidx]));
           const double* y = a.tape.ys + ((size_t)cell * a.tape.cap_steps + sidx) * S;
           for (int i = threadIdx.x; i < S; i += NT) {
             s.y[i] = y[i];
@@ -234,6 +241,7 @@ __global__ void __launch_bounds__(NT, 1) grad_kernel(const GradArgs a) {
           }
           __syncthreads();
         } else {  // init
+          if (a.track) rates_for(track_params(a.track, a.K, cell, a.t0));
           nu_transpose(n, Lam + S, g);
           grad_accumulate(n, kap, dT, s.tmp, g, v, grow, s.red, &gnH, &gT);
         }

@@ -123,6 +123,11 @@ struct cbx_tape {
   cbx_cell_params* phi = nullptr;  // [C] copy of the recorded solve's parameters
   double* x0 = nullptr;            // [S][C] copy of its initial abundances
   int* status = nullptr;           // [C] its cell status
+  double* alpha = nullptr;         // [R] the alpha values the recorded solve used
+  double* track = nullptr;         // [C][K][6] copy of the recorded solve's tracks (own allocation)
+  size_t track_cap = 0;            // doubles allocated at track
+  int K = 0;                       // 0: the recorded solve had a constant environment
+  double t0 = 0.0;
   int recorded_C = 0;
 };
 
@@ -220,7 +225,7 @@ int cbx_network_symbolic(const cbx_network* net, int* perm, unsigned char* fill,
 static int solve_impl(cbx_network* net, const cbx_cell_params* phi, const double* x0, int C, double t0,
                       double t_end, const cbx_options* opt, void* stream, double* x_out, int* cell_status,
                       cbx_cell_stats* stats, cbx_tape* tape, int max_grid = 0, const double* track = nullptr,
-                      int K = 0) {
+                      int K = 0, const double* alpha = nullptr) {
   if (!net) return fail(CBX_E_ARG, "net is NULL");
   if (C < 0) return fail(CBX_E_ARG, "C must be >= 0");
   if (C > 0 && ((!phi && !track) || !x0 || !x_out || !cell_status)) return fail(CBX_E_ARG, "NULL array with C > 0");
@@ -248,7 +253,7 @@ static int solve_impl(cbx_network* net, const cbx_cell_params* phi, const double
   cudaStream_t st = (cudaStream_t)stream;
   SolveArgs a{};
   a.net = net->dev;
-  a.alpha = net->dev.alpha;
+  a.alpha = alpha ? alpha : net->dev.alpha;
   a.phi = phi;
   a.track = track;
   a.K = K;
@@ -284,10 +289,32 @@ static int solve_impl(cbx_network* net, const cbx_cell_params* phi, const double
   if (e != cudaSuccess) return cuda_fail(e, "solver launch");
   if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync(workspace)");
   if (tape) {
-    e = cudaMemcpyAsync(tape->phi, phi, C * sizeof(cbx_cell_params), cudaMemcpyDeviceToDevice, st);
+    e = cudaSuccess;
+    if (track) {
+      const size_t nd = (size_t)C * K * 6;
+      if (tape->track_cap < nd) {
+        if (tape->track) {
+          cudaStreamSynchronize(st);
+          cudaFree(tape->track);
+          tape->track = nullptr;
+          tape->track_cap = 0;
+        }
+        e = cudaMalloc(&tape->track, nd * sizeof(double));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(tape track)");
+        tape->track_cap = nd;
+      }
+      e = cudaMemcpyAsync(tape->track, track, nd * sizeof(double), cudaMemcpyDeviceToDevice, st);
+      tape->K = K;
+    } else {
+      e = cudaMemcpyAsync(tape->phi, phi, C * sizeof(cbx_cell_params), cudaMemcpyDeviceToDevice, st);
+      tape->K = 0;
+    }
+    tape->t0 = t0;
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(tape->x0, x0, (size_t)h.S * C * sizeof(double), cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(tape->status, cell_status, C * sizeof(int), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && h.R > 0)
+      e = cudaMemcpyAsync(tape->alpha, a.alpha, (size_t)h.R * sizeof(double), cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(tape copies)");
     tape->recorded_C = C;
   }
@@ -386,8 +413,10 @@ int cbx_tape_create(cbx_network* net, int C, int max_steps, cbx_tape** out) {
   const size_t n_ops = (size_t)C * t->dev.cap_ops;
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
   const size_t o_nops = 0, o_kq = o_nops + al(C * 4), o_v = o_kq + al(n_ops * 4), o_y = o_v + al(n_ops * 8),
-               o_phi = o_y + al((size_t)C * max_steps * t->S * 8), o_x0 = o_phi + al(C * sizeof(cbx_cell_params)),
-               o_st = o_x0 + al((size_t)t->S * C * 8), total = o_st + al(C * 4);
+               o_ts = o_y + al((size_t)C * max_steps * t->S * 8), o_phi = o_ts + al((size_t)C * max_steps * 8),
+               o_x0 = o_phi + al(C * sizeof(cbx_cell_params)),
+               o_st = o_x0 + al((size_t)t->S * C * 8), o_al = o_st + al(C * 4),
+               total = o_al + al((size_t)net->host.R * 8 + 8);
   cudaError_t e = cudaMalloc(&t->dbuf, total);
   if (e != cudaSuccess) {
     delete t;
@@ -398,9 +427,11 @@ int cbx_tape_create(cbx_network* net, int C, int max_steps, cbx_tape** out) {
   t->dev.ops_kq = (int*)(b + o_kq);
   t->dev.ops_v = (double*)(b + o_v);
   t->dev.ys = (double*)(b + o_y);
+  t->dev.ts = (double*)(b + o_ts);
   t->phi = (cbx_cell_params*)(b + o_phi);
   t->x0 = (double*)(b + o_x0);
   t->status = (int*)(b + o_st);
+  t->alpha = (double*)(b + o_al);
   e = cudaMemset(t->dev.nops, 0, C * sizeof(int));
   if (e != cudaSuccess) {
     cudaFree(t->dbuf);
@@ -414,6 +445,7 @@ int cbx_tape_create(cbx_network* net, int C, int max_steps, cbx_tape** out) {
 int cbx_tape_destroy(cbx_tape* tape) {
   if (!tape) return CBX_OK;
   if (tape->dbuf) cudaFree(tape->dbuf);
+  if (tape->track) cudaFree(tape->track);
   delete tape;
   return CBX_OK;
 }
@@ -425,6 +457,50 @@ int cbx_solve_record(cbx_network* net, const cbx_cell_params* phi, const double*
   if (tape->net != net) return fail(CBX_E_ARG, "the tape belongs to another network");
   if (C > tape->C) return fail(CBX_E_ARG, "C exceeds the tape's capacity");
   return solve_impl(net, phi, x0, C, t0, t_end, opt, stream, x_out, cell_status, stats, tape);
+}
+
+int cbx_solve_with_alpha(cbx_network* net, const double* alpha, const cbx_cell_params* phi, const double* x0, int C,
+                         double t0, double t_end, const cbx_options* opt, void* stream, double* x_out,
+                         int* cell_status, cbx_cell_stats* stats, cbx_tape* tape) {
+  if (!alpha && net && net->host.R > 0) return fail(CBX_E_ARG, "alpha is NULL");
+  if (tape) {
+    if (tape->net != net) return fail(CBX_E_ARG, "the tape belongs to another network");
+    if (C > tape->C) return fail(CBX_E_ARG, "C exceeds the tape's capacity");
+  }
+  return solve_impl(net, phi, x0, C, t0, t_end, opt, stream, x_out, cell_status, stats, tape, 0, nullptr, 0, alpha);
+}
+
+int cbx_solve_track_record(cbx_network* net, const double* track, int K, const double* x0, int C, double t0,
+                           double t_end, const cbx_options* opt, void* stream, double* x_out, int* cell_status,
+                           cbx_cell_stats* stats, cbx_tape* tape) {
+  if (!tape) return fail(CBX_E_ARG, "tape is NULL");
+  if (tape->net != net) return fail(CBX_E_ARG, "the tape belongs to another network");
+  if (C > tape->C) return fail(CBX_E_ARG, "C exceeds the tape's capacity");
+  if (K < 1) return fail(CBX_E_ARG, "K must be >= 1");
+  if (C > 0 && !track) return fail(CBX_E_ARG, "track is NULL");
+  return solve_impl(net, nullptr, x0, C, t0, t_end, opt, stream, x_out, cell_status, stats, tape, 0, track, K);
+}
+
+int cbx_tape_step_times(const cbx_tape* tape, int cell, double* t_new, int cap) {
+  if (!tape || cell < 0 || cell >= tape->C || cap < 0) return fail(CBX_E_ARG, "bad argument");
+  int nops = 0;
+  cudaError_t e = cudaMemcpy(&nops, tape->dev.nops + cell, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(tape)");
+  std::vector<int> kq(nops);
+  if (nops > 0) {
+    e = cudaMemcpy(kq.data(), tape->dev.ops_kq + (size_t)cell * tape->dev.cap_ops, nops * sizeof(int),
+                   cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(tape)");
+  }
+  int n = 0;
+  for (int v : kq) n += (v >> 8) == kOpStep;
+  const int m = std::min(n, cap);
+  if (m > 0 && t_new) {
+    e = cudaMemcpy(t_new, tape->dev.ts + (size_t)cell * tape->dev.cap_steps, m * sizeof(double),
+                   cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(tape)");
+  }
+  return n;
 }
 
 int cbx_grad(cbx_tape* tape, const double* cot_x, void* stream, double* g_logalpha, double* g_lognH,
@@ -446,9 +522,12 @@ int cbx_grad_env(cbx_tape* tape, const double* cot_x, void* stream, double* g_lo
   cudaStream_t st = (cudaStream_t)stream;
   GradArgs a{};
   a.net = net->dev;
-  a.alpha = net->dev.alpha;
+  a.alpha = tape->alpha;
   a.tape = tape->dev;
-  a.phi = tape->phi;
+  a.phi = tape->K > 0 ? nullptr : tape->phi;
+  a.track = tape->K > 0 ? tape->track : nullptr;
+  a.K = tape->K;
+  a.t0 = tape->t0;
   a.status = tape->status;
   a.x0 = tape->x0;
   a.cot = cot_x;

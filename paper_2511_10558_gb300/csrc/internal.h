@@ -63,6 +63,7 @@ struct TapeDev {
   int* ops_kq = nullptr;   // [C][cap_ops] (kind << 8) | q; kind 0 init, 1 rescale, 2 step
   double* ops_v = nullptr; // [C][cap_ops] h0 (init), rho (rescale), h (step)
   double* ys = nullptr;    // [C][cap_steps][S] step results, internal species order
+  double* ts = nullptr;    // [C][cap_steps] t_new of each recorded step
 };
 
 enum { kOpInit = 0, kOpRescale = 1, kOpStep = 2 };
@@ -118,7 +119,10 @@ struct GradArgs {
   DevNet net;
   const double* alpha;  // [R] device: the alpha values of the recorded solve
   TapeDev tape;
-  const cbx_cell_params* phi;  // [C] as recorded
+  const cbx_cell_params* phi;  // [C] as recorded (constant environment), or null with a track
+  const double* track;         // [C][K][6] the recorded solve's environment tracks, or null
+  int K;
+  double t0;                   // start time of the recorded solve
   const int* status;           // [C] forward status
   const double* x0;            // [S][C] as recorded (user order)
   const double* cot;           // [S][C] dL/dx(t_end) (user order)

@@ -1139,7 +1139,8 @@ __device__ void rec_op(const SolveArgs& a, int cell, Recorder& r, int kind, int 
   r.nops++;
 }
 
-__device__ void rec_step(const SolveArgs& a, int cell, Recorder& r, int q, double h, const double* y, int S) {
+__device__ void rec_step(const SolveArgs& a, int cell, Recorder& r, int q, double h, double t_new, const double* y,
+                         int S) {
   if (!r.on || r.full) return;
   if (r.nops >= a.tape.cap_ops || r.nsteps >= a.tape.cap_steps) {
     r.full = true;
@@ -1147,6 +1148,7 @@ __device__ void rec_step(const SolveArgs& a, int cell, Recorder& r, int q, doubl
   }
   double* dst = a.tape.ys + ((size_t)cell * a.tape.cap_steps + r.nsteps) * S;
   for (int i = threadIdx.x; i < S; i += NT) dst[i] = y[i];
+  if (threadIdx.x == 0) a.tape.ts[(size_t)cell * a.tape.cap_steps + r.nsteps] = t_new;
   rec_op(a, cell, r, kOpStep, q, h);
   r.nsteps++;
 }
@@ -1155,12 +1157,12 @@ __device__ void rec_step(const SolveArgs& a, int cell, Recorder& r, int q, doubl
 // k = 0..K-1: linear between knots, the end values outside [t_0, t_{K-1}]
 // (the phi(t) of the generalised system of Sec. 2; x is per n_H, so a
 // changing n_H enters only the two-body coefficients).
-__device__ cbx_cell_params track_params(const SolveArgs& a, int cell, double t) {
-  const double* k0 = a.track + (size_t)cell * a.K * 6;
+__device__ cbx_cell_params track_params(const double* track, int K, int cell, double t) {
+  const double* k0 = track + (size_t)cell * K * 6;
   int k = 0;
-  while (k + 1 < a.K && k0[(k + 1) * 6] <= t) ++k;
+  while (k + 1 < K && k0[(k + 1) * 6] <= t) ++k;
   const double* A = k0 + k * 6;
-  if (k + 1 >= a.K || t <= A[0]) return cbx_cell_params{A[1], A[2], A[3], A[4], A[5]};
+  if (k + 1 >= K || t <= A[0]) return cbx_cell_params{A[1], A[2], A[3], A[4], A[5]};
   const double* B = A + 6;
   const double w = (t - A[0]) / (B[0] - A[0]);
   return cbx_cell_params{fma(w, B[1] - A[1], A[1]), fma(w, B[2] - A[2], A[2]), fma(w, B[3] - A[3], A[3]),
@@ -1193,7 +1195,7 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
     c.st->t_begin_ns = (long long)globaltimer();
   }
   int attempts = 0;
-  const cbx_cell_params p = a.track ? track_params(a, cell, a.t0) : a.phi[cell];
+  const cbx_cell_params p = a.track ? track_params(a.track, a.K, cell, a.t0) : a.phi[cell];
   int status = CBX_CELL_OK;
   Recorder rec;
   rec.on = a.tape.nops != nullptr;
@@ -1210,7 +1212,7 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
     double t_rates = a.t0;
     auto rates_at = [&](double tt) {
       if (a.track && tt != t_rates) {
-        rate_coefficients(n, a.alpha, track_params(a, cell, tt), c.kap);
+        rate_coefficients(n, a.alpha, track_params(a.track, a.K, cell, tt), c.kap);
         __syncthreads();
         t_rates = tt;
       }
@@ -1324,7 +1326,7 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
         accepted = true;
       }
       if (!accepted) break;
-      rec_step(a, cell, rec, q, h, s.y, S);
+      rec_step(a, cell, rec, q, h, t_new, s.y, S);
       if (threadIdx.x == 0) c.st->steps++;
       t = t_new;
       jac_current = false;

@@ -10,8 +10,9 @@ abundances with a Gaussian prior around the network's own values:
              + sum_j (theta_j - theta0_j)^2 / (2 s_j^2),
 
 x_ci the abundance of target species i of cell c at t_end. grad U comes from
-one recorded forward solve and the discrete adjoint (cbx_solve_record and
-cbx_grad: dL/d ln alpha summed over cells) -- the derivative of the discrete
+one recorded forward solve with alpha = exp(theta) passed for that call only
+(cbx_solve_with_alpha: the network is not modified) and the discrete adjoint
+(cbx_grad: dL/d ln alpha summed over cells) -- the derivative of the discrete
 map with its step program frozen. Sampling: leapfrog integration of
 H = U + |p|^2 / 2 with unit mass, step eps, L steps, then Metropolis acceptance
 of the endpoint (Duane, Kennedy, Pendleton & Roweth 1987; Neal 2011).
@@ -69,8 +70,8 @@ class RatePosterior:
         import torch
         cb = self.carbox
         theta = np.asarray(theta, dtype=float)
-        self.net.set_alpha(np.exp(theta))
-        x, st = cb.solve_record(self.net, self.tape, self.phi, self.x0, 0.0, self.t_end, self.opt)
+        alpha = torch.tensor(np.exp(theta), dtype=torch.float64, device=self.phi.device)
+        x, st = cb.solve_with_alpha(self.net, alpha, self.phi, self.x0, 0.0, self.t_end, self.opt, tape=self.tape)
         xh = x.cpu().numpy()
         if not bool((st == 0).all().item()):
             return np.inf, np.zeros_like(theta)

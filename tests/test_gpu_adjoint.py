@@ -172,6 +172,34 @@ def test_autograd_function(dev, net32):
     torch.testing.assert_close(T.grad, gt, rtol=1e-6, atol=1e-12)
 
 
+def test_cell_solve_leaves_the_network_alone(dev, net32):
+    # the autograd Function passes alpha for its call only: a plain solve on the
+    # same Network afterwards returns the original result, and the Function's
+    # result equals a solve of a separate network that holds those alpha values
+    N = carbox.Network.from_synth(net32)
+    Cn = 3
+    phi = synth.cells(Cn, seed=5)
+    phi_d = torch.tensor(phi, device=dev).contiguous()
+    x0 = torch.tensor(np.repeat(synth.initial_abundances(net32)[:, None], Cn, axis=1), device=dev).contiguous()
+    t_end = 1e5 * YR
+    base, _, _ = carbox.solve(N, phi_d, x0, 0.0, t_end)
+    base = base.cpu().numpy()
+    la = torch.tensor(np.log(net32.alpha) + np.linspace(-0.4, 0.4, net32.n_reactions), device=dev,
+                      requires_grad=True)
+    lnH = torch.tensor(np.log(phi[:, 0]), device=dev)
+    lx = carbox.cell_solve(la, lnH, torch.tensor(phi[:, 1], device=dev), N, x0,
+                           torch.tensor(phi[:, 2:], device=dev).contiguous(), t_end)
+    after, _, _ = carbox.solve(N, phi_d, x0, 0.0, t_end)
+    np.testing.assert_array_equal(after.cpu().numpy(), base)
+    other = adj.with_alpha(net32, torch.exp(la.detach()).cpu().numpy())
+    N2 = carbox.Network.from_synth(other)
+    phi2 = phi_d.clone()
+    phi2[:, 0] = torch.exp(lnH)
+    x2, _, _ = carbox.solve(N2, phi2.contiguous(), x0, 0.0, t_end)
+    np.testing.assert_array_equal(torch.log10(x2).cpu().numpy(), lx.detach().cpu().numpy())
+    assert np.max(np.abs(lx.detach().cpu().numpy() - np.log10(base))) > 1e-3  # the other alpha mattered
+
+
 def test_environment_gradients(dev, net32):
     # cbx_grad_env: d/d ln zeta, d/d ln G0, d/dA_V of the GPU program against
     # (a) the oracle's adjoint of the same program mapped by

@@ -87,3 +87,73 @@ def test_bad_track_and_arguments(dev, net32):
     with pytest.raises(RuntimeError):
         carbox.solve_track(N, torch.zeros((3, 0, 6), dtype=torch.float64, device=dev),
                            torch.tensor(x0, device=dev).contiguous(), 0.0, t_end)
+
+
+def test_track_gradients_match_oracle_adjoint(dev, net32):
+    # gradients through phi(t): the reverse sweep re-evaluates the coefficients
+    # at every recorded step time; compared with the oracle's adjoint of the
+    # same program (step times read back from the tape) and with central
+    # differences of its exact replay (common n_H factor, common T shift)
+    from oracle import adjoint as adj
+    t_end = 1e5 * YR
+    C = 2
+    phi = synth.cells(C, seed=9)
+    tr = synth.tracks(phi, t_end)
+    x0 = np.repeat(synth.initial_abundances(net32)[:, None], C, axis=1)
+    N = carbox.Network.from_synth(net32)
+    tr_d = torch.tensor(tr, device=dev).contiguous()
+    x0_d = torch.tensor(x0, device=dev).contiguous()
+    tape = carbox.Tape(N, C, 4000)
+    x, st = carbox.solve_track_record(N, tape, tr_d, x0_d, 0.0, t_end)
+    xp, _, _ = carbox.solve_track(N, tr_d, x0_d, 0.0, t_end)
+    np.testing.assert_array_equal(x.cpu().numpy(), xp.cpu().numpy())  # recording does not change the solve
+    xh = x.cpu().numpy()
+    assert np.all(st.cpu().numpy() == carbox.CBX_CELL_OK)
+    rng = np.random.default_rng(4)
+    tgs, yts, cot = [], [], np.zeros_like(xh)
+    for c in range(C):
+        tg = np.sort(rng.choice(np.flatnonzero(xh[:, c] > 1e-12), 8, replace=False))
+        yt = np.log10(xh[tg, c]) + rng.uniform(-0.5, 0.5, len(tg))
+        tgs.append(tg)
+        yts.append(yt)
+        cot[:, c] = adj.log10_loss(xh[:, c], tg, yt)[1]
+    ga, gn, gt, gz, gg, gav = [o.cpu().numpy() for o in
+                               carbox.grad_env(tape, torch.tensor(cot, device=dev).contiguous(), C)]
+    ga_ref = np.zeros(net32.n_reactions)
+    for c in range(C):
+        ts = tape.step_times(c)
+        prog, k = [], 0
+        for kind, q, v in tape.program(c):
+            if kind == 2:
+                prog.append(("step", q, v, ts[k], None))
+                k += 1
+            else:
+                prog.append(("init", v) if kind == 0 else ("rescale", q, v))
+        assert k == len(ts) and ts[-1] == t_end
+        x_rep, prog_rep = adj.replay(net32, None, x0[:, c], prog, track=tr[c])
+        _, cot_rep = adj.log10_loss(x_rep, tgs[c], yts[c])
+        g_la, g_nH, g_T = adj.adjoint(net32, None, x0[:, c], prog_rep, cot_rep, track=tr[c])
+        ga_ref += g_la
+        assert gn[c] == pytest.approx(g_nH, rel=1e-3)
+        assert gt[c] == pytest.approx(g_T, rel=1e-3)
+        z, g0, av = adj.environment_gradients(net32, g_la)
+        assert gz[c] == pytest.approx(z, rel=1e-3) and gg[c] == pytest.approx(g0, rel=1e-3)
+        assert gav[c] == pytest.approx(av, rel=1e-3)
+        if c == 0:
+            eps = 1e-6
+
+            def loss(track):
+                xr, _ = adj.replay(net32, None, x0[:, 0], prog, track=track)
+                return adj.log10_loss(xr, tgs[0], yts[0])[0]
+
+            tp, tm = tr[0].copy(), tr[0].copy()
+            tp[:, 1] *= np.exp(eps)
+            tm[:, 1] *= np.exp(-eps)
+            assert (loss(tp) - loss(tm)) / (2 * eps) == pytest.approx(gn[0], rel=1e-3)
+            d = eps * tr[0, 0, 2]
+            tp, tm = tr[0].copy(), tr[0].copy()
+            tp[:, 2] += d
+            tm[:, 2] -= d
+            assert (loss(tp) - loss(tm)) / (2 * d) == pytest.approx(gt[0], rel=1e-3)
+    big = np.abs(ga_ref) > 1e-6 * np.abs(ga_ref).max()
+    assert np.all(np.abs(ga[big] - ga_ref[big]) <= 1e-3 * np.abs(ga_ref[big]))
