@@ -9,9 +9,20 @@ plain FP64. One step = one solve of the whole batch.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                     [--cells C] [--only fp64|mixed] [--no-e2e] [--no-cpu-baseline]
+                    [--no-large] [--no-extras] [--config large|adjoint|serving|zeta|track|peaks]
 
-(--cells / --only / --no-e2e shrink the run for profiler captures; the default
-run is the benchmark.)
+(--cells / --only / --no-e2e / --no-large / --no-extras shrink the run for
+profiler captures; the default run is the benchmark.)
+
+Besides the headline (FP64) the default line carries: the mixed-precision
+path on the same cells; the measured FP64 and FP32 FMA peaks (the library's
+probe kernel, run in this job) that the ALU rooflines divide by; 500 species /
+6000 reactions in both precisions on the same 4,096 cells with the per-species
+error against the FP64 oracle; the oracle parity sample with the converged
+gate for cells on another step program; and compact runs of the adjoint
+(1,024 cells, 1e5 yr), serving (Poisson requests at 200/s), time-dependent
+environment tracks and the cosmic-ray sweep with sensitivities, all under the
+same clock record.
 
 With N > 1 (torchrun) each rank solves its own 16,384 cells of a batch of
 N x 16,384 (weak scaling, no collective on the data path); the barrier and the
@@ -41,7 +52,8 @@ S_SP, R_RX = 150, 1500
 CELLS = 16384  # per GPU (overridden by --cells for profiler captures)
 T_END = 1e6 * synth.YEAR
 RTOL, ATOL = 1e-4, 1e-20
-FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (152 SMs x 2 FMA/clk x 2.07 GHz); 1.19 measured by FMA chains
+FP64_NOMINAL_TFLOPS = 1.26  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (used only if the probe fails)
+FP32_NOMINAL_TFLOPS = 80.5  # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz (used only if the probe fails)
 
 
 # ------------------------------------------------------------------ helpers
@@ -122,6 +134,59 @@ def algorithmic_flops(info, st, R_two, R_one, n_nu):
             "refine_fp64": ref * 2.0 * info["nnz_jac"], "refine_fp32": ref * 2.0 * info["nnz_lu"]}
 
 
+def mixed_flops(info, st, R_two, R_one, n_nu):
+    """(FP32, FP64) flops of the mixed path: the LU and every triangular-solve
+    pair (the first solve of each Newton iteration and each refinement sweep)
+    in FP32; rates, right-hand sides, Jacobians and the refinement residuals
+    in FP64."""
+    fl = algorithmic_flops(info, st, R_two, R_one, n_nu)
+    sweeps = st["refine_sweeps"].astype(np.float64).sum()
+    fp32 = fl["lu"] + fl["solve"] + sweeps * 2.0 * info["nnz_lu"]
+    fp64 = fl["rhs"] + fl["jac"] + fl["refine_fp64"]
+    return fp32, fp64
+
+
+def measure_fma_peaks(carbox, dev, stream):
+    """FP64 and FP32 FMA peaks (TFLOP/s, best of 3 launches) from the library's
+    probe kernel: 8 CTAs of 256 threads per SM, 8 independent FMA chains each."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    grid, block = sms * 8, 256
+    sink = torch.zeros(grid, dtype=torch.float64, device=dev)
+    out = {"how": f"cbx_peak_fma: {grid} CTAs x {block} threads x 8 dependent-FMA chains, best of 3, CUDA events"}
+    for name, fp64, iters in (("fp64", 1, 40000), ("fp32", 0, 2000000)):
+        flops = carbox.lib.cbx_peak_fma_flops(grid, block, iters)
+        best = 0.0
+        for _ in range(4):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc = carbox.lib.cbx_peak_fma(fp64, grid, block, iters, carbox.C.c_void_p(stream.cuda_stream),
+                                         carbox.C.c_void_p(sink.data_ptr()))
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            if rc != 0:
+                return None
+            best = max(best, flops / (e0.elapsed_time(e1) / 1e3) / 1e12)
+        out[name + "_tflops"] = best
+    return out
+
+
+def _oracle_job(args):
+    net, phi, x0, t_end, rtol, atol = args
+    from oracle import bdf
+    return bdf.solve_cell(net, phi, x0, 0.0, t_end, rtol, atol).x
+
+
+def oracle_map(net, phis, x0, t_end, rtol=RTOL, atol=ATOL):
+    """Oracle results [S, n] for the cells phis (x0 shared), one spawn process per host core."""
+    ctx = mp.get_context("spawn")
+    n = len(phis)
+    os.environ["OPENBLAS_NUM_THREADS"] = os.environ["OMP_NUM_THREADS"] = "1"
+    with ctx.Pool(max(1, min(n, os.cpu_count() or 1))) as pool:
+        out = pool.map(_oracle_job, [(net, phis[i], x0, t_end, rtol, atol) for i in range(n)])
+    return np.stack(out, axis=1)
+
+
 def flush_l2(buf):
     buf.add_(1.0)
 
@@ -191,16 +256,27 @@ def time_oracle(n_cells, cores):
     return n_cells / dt, dt, xs
 
 
-def parity_summary(x_gpu, x_ref, tol=1e-4, floor=1e-12):
+def parity_summary(x_gpu, x_ref, tol=1e-4, floor=1e-12, tight=None):
     """Per sampled cell, the largest relative difference over species above
-    `floor`; how many cells are within `tol`."""
+    `floor`; how many cells are within `tol`. tight: {cell: rtol-1e-8 oracle
+    result} for the cells outside tol, which then get the converged gate (the
+    GPU's error against that reference at most twice the oracle's own)."""
     rel = []
     for c in range(x_ref.shape[1]):
         big = x_ref[:, c] > floor
         rel.append(float(np.max(np.abs(x_gpu[big, c] / x_ref[big, c] - 1))) if big.any() else 0.0)
     rel = np.array(rel)
-    return {"cells": int(rel.size), "tol": tol, "within_tol": int((rel <= tol).sum()),
-            "max_rel": float(rel.max()), "median_rel": float(np.median(rel))}
+    out = {"cells": int(rel.size), "tol": tol, "within_tol": int((rel <= tol).sum()),
+           "max_rel": float(rel.max()), "median_rel": float(np.median(rel)), "converged_gate": []}
+    for c, ref8 in (tight or {}).items():
+        big = ref8 > floor
+        e_gpu = float(np.max(np.abs(x_gpu[big, c] / ref8[big] - 1)))
+        e_orc = float(np.max(np.abs(x_ref[big, c] / ref8[big] - 1)))
+        out["converged_gate"].append({"cell": int(c), "twin_rel": float(rel[c]), "err_gpu_vs_rtol1e-8": e_gpu,
+                                      "err_oracle_vs_rtol1e-8": e_orc, "pass": e_gpu <= 2.0 * e_orc})
+    out["all_pass_gate"] = bool(all(g["pass"] for g in out["converged_gate"]) and
+                                out["within_tol"] + len(out["converged_gate"]) == out["cells"])
+    return out
 
 
 def run_reference(args):
@@ -287,6 +363,17 @@ def run_gpu(args):
         ms = [a.elapsed_time(b) for a, b in ev]
         return ms
 
+    # ---- measured FMA peaks (the ALU roofline denominators), before the timed work
+    peaks = None
+    if rank == 0 and not args.no_peaks:
+        with ClockSampler(local) as clk_peaks:
+            peaks = measure_fma_peaks(carbox, dev, stream)
+        if peaks is not None:
+            peaks["clocks"] = clk_peaks.summary()
+    fp64_peak = peaks["fp64_tflops"] if peaks else FP64_NOMINAL_TFLOPS
+    fp32_peak = peaks["fp32_tflops"] if peaks else FP32_NOMINAL_TFLOPS
+    peak_src = "measured in this run (FMA-chain probe)" if peaks else "nominal (probe unavailable)"
+
     # ---- FP64 (headline)
     with ClockSampler(local) as clk:
         ms64 = timed(carbox.CBX_FP64, args.steps, args.warmup) if args.only != "mixed" else [float("nan")]
@@ -306,7 +393,8 @@ def run_gpu(args):
     if args.only == "fp64":
         print(json.dumps({"only": "fp64", "cells": CELLS, "ms_per_step": ms_per_step, "value": value}), flush=True)
         return
-    msmx = timed(carbox.CBX_MIXED, max(1, args.steps), 1 if args.only != "mixed" else args.warmup)
+    with ClockSampler(local) as clk_mx:
+        msmx = timed(carbox.CBX_MIXED, max(1, args.steps), 1 if args.only != "mixed" else args.warmup)
     if args.only == "mixed":
         print(json.dumps({"only": "mixed", "cells": CELLS, "ms_per_step": sum(msmx) / len(msmx),
                           "value": CELLS * len(msmx) / (sum(msmx) / 1e3)}), flush=True)
@@ -314,13 +402,18 @@ def run_gpu(args):
     stmx = carbox.stats_dict(stats.cpu().numpy())
     okmx = int((status == 0).sum().item())
     xmx_sample = x_out[:, :n_sample].cpu().numpy()
+    ms_mx = sum(msmx) / len(msmx)
     mixed_value = CELLS * len(msmx) / (sum(msmx) / 1e3)
     latmx = (stmx["t_end_ns"] - stmx["t_begin_ns"]) / 1e6
+    f32, f64mx = mixed_flops(info, stmx, R_two, R_one, n_nu)
+    ach32, ach64mx = f32 / (ms_mx / 1e3) / 1e12, f64mx / (ms_mx / 1e3) / 1e12
 
     # ---- 500 species / 6000 reactions (matrix in the CTAs' global workspace)
     large = None
     if not args.no_large and ws == 1:
-        large = run_large_throughput(carbox, dev, stream, 4096, 608)
+        with ClockSampler(local) as clk_l:
+            large = run_large_throughput(carbox, dev, stream, 4096, errors=rank == 0 and not args.no_cpu_baseline)
+        large["clocks"] = clk_l.summary()
 
     # ---- end to end through the host-buffer C-ABI call (copies inside the timed region)
     opt = carbox.options(rtol=RTOL, atol=ATOL, precision=carbox.CBX_FP64)
@@ -342,8 +435,27 @@ def run_gpu(args):
         v, dt, x_ref = time_oracle(ncell, cores)
         cpu = {"value": v, "unit": "cell-solves/s", "cores": cores, "kind": "oracle",
                "sample": f"first {ncell} of the {CELLS} seeded cells, spawn pool of {cores} processes, {dt:.1f} s"}
-        parity = {"fp64": parity_summary(x64_sample[:, :ncell], x_ref),
-                  "mixed": parity_summary(xmx_sample[:, :ncell], x_ref)}
+        # cells outside 1e-4 in either precision get the converged gate (rtol-1e-8 oracle reference)
+        out_tol = sorted(set(c for xs in (x64_sample, xmx_sample) for c in range(ncell)
+                             if parity_summary(xs[:, c:c + 1], x_ref[:, c:c + 1])["within_tol"] == 0))
+        tight = {}
+        if out_tol:
+            phis = synth.cells(CELLS)[out_tol]
+            refs = oracle_map(net, phis, synth.initial_abundances(net), T_END, 1e-8, 1e-26)
+            tight = {c: refs[:, k] for k, c in enumerate(out_tol)}
+        parity = {}
+        for name, xs in (("fp64", x64_sample), ("mixed", xmx_sample)):
+            t_sub = {c: r for c, r in tight.items()
+                     if parity_summary(xs[:, c:c + 1], x_ref[:, c:c + 1])["within_tol"] == 0}
+            parity[name] = parity_summary(xs[:, :ncell], x_ref, tight=t_sub)
+    extras = None
+    if ws == 1 and not args.no_extras:
+        with ClockSampler(local) as clk_x:
+            extras = {"adjoint": adjoint_block(carbox, dev, stream, checks=1),
+                      "serving": serving_block(carbox, rate=200.0, duration=0.25),
+                      "track": track_block(carbox, dev, stream, checks=1),
+                      "zeta": zeta_block(carbox, dev, stream, checks=1)}
+        extras["clocks"] = clk_x.summary()
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     traffic = None
     if os.path.exists(prof):
@@ -362,21 +474,30 @@ def run_gpu(args):
                        "batch_p50": float(np.percentile(ms64, 50)), "batch_max": float(max(ms64))},
         "cells_ok": ok64,
         "mixed": {"value": mixed_value, "unit": "cell-solves/s", "dtype": "f64 state + f32 LU",
-                  "ms_per_step": sum(msmx) / len(msmx), "speedup_vs_fp64": mixed_value / (value / ws),
+                  "ms_per_step": ms_mx, "speedup_vs_fp64": mixed_value / (value / ws),
                   "cells_ok": okmx, "cell_p50_ms": float(np.percentile(latmx, 50)),
                   "cell_p99_ms": float(np.percentile(latmx, 99)),
-                  "mean_refine_sweeps_per_newton": float(stmx["refine_sweeps"].sum() / max(1, stmx["newton_iters"].sum()))},
+                  "mean_refine_sweeps_per_newton": float(stmx["refine_sweeps"].sum() / max(1, stmx["newton_iters"].sum())),
+                  "roofline": {"bound": "alu", "kernel": "solve_kernel<float> (FP32 LU and solves, FP64 rest)",
+                               "fp32": {"achieved": ach32, "peak": fp32_peak, "unit": "TFLOP/s",
+                                        "frac": ach32 / fp32_peak, "flops_per_launch": f32},
+                               "fp64": {"achieved": ach64mx, "peak": fp64_peak, "unit": "TFLOP/s",
+                                        "frac": ach64mx / fp64_peak, "flops_per_launch": f64mx},
+                               "peak_source": peak_src},
+                  "clocks": clk_mx.summary()},
         "large_500": large,
         "counters_per_cell": {k: float(st64[k].mean()) for k in carbox.STATS_FIELDS},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp64_peak, "traffic": traffic, "peak_source": peak_src,
                      "kernel": "solve_kernel<double> (FP64 pipe)",
                      "flops_per_launch": fp64_flops, "flop_split": {k: v for k, v in fl.items()}},
+        "peaks": peaks,
         "cpu_baseline": cpu,
         "parity_sample": parity,
         "e2e": {"value": e2e_value, "unit": "cell-solves/s",
                 "h2d_bytes_per_step": int(phi_h.nbytes + x0_h.nbytes),
                 "d2h_bytes_per_step": int(x0_h.nbytes + CELLS * 4)},
+        "configs": extras,
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
     }
@@ -393,78 +514,79 @@ def _gpu_setup():
     return torch, dev, carbox
 
 
-def run_large_throughput(carbox, dev, stream, cells_mixed, cells_fp64):
-    """500 species / 6000 reactions, 1 Myr: mixed and FP64 cell-solves/s (one timed step each)."""
+def run_large_throughput(carbox, dev, stream, cells, errors=True, n_err=4):
+    """500 species / 6000 reactions, 1 Myr: mixed and FP64 cell-solves/s on the same
+    `cells` seeded cells (one timed step each), and (errors) the per-species
+    relative error of both against the FP64 oracle on the first n_err cells
+    (species above 1e-12), with element and charge conservation."""
     import torch
     net = synth.make_network(500, 6000)
     N = carbox.Network.from_synth(net)
-    out = {"workload": "500 species / 6000 reactions (seed 1500), 1 Myr, rtol 1e-4, atol 1e-20"}
-    for name, prec, C in [("mixed", carbox.CBX_MIXED, cells_mixed), ("fp64", carbox.CBX_FP64, cells_fp64)]:
-        phi = torch.tensor(synth.cells(C), device=dev)
-        x0 = torch.tensor(np.repeat(synth.initial_abundances(net)[:, None], C, axis=1), device=dev).contiguous()
-        st = carbox.stats_tensor(C, dev)
+    phi_h = synth.cells(cells)
+    x0_h = np.repeat(synth.initial_abundances(net)[:, None], cells, axis=1)
+    phi = torch.tensor(phi_h, device=dev)
+    x0 = torch.tensor(x0_h, device=dev).contiguous()
+    out = {"workload": f"500 species / 6000 reactions (seed 1500), {cells} cells (the same for both precisions), "
+                       "1 Myr, rtol 1e-4, atol 1e-20"}
+    xs = {}
+    for name, prec in [("mixed", carbox.CBX_MIXED), ("fp64", carbox.CBX_FP64)]:
+        st = carbox.stats_tensor(cells, dev)
         o = carbox.options(rtol=RTOL, atol=ATOL, precision=prec)
         carbox.solve(N, phi[:152].contiguous(), x0[:, :152].contiguous(), 0.0, T_END, o, stream=stream)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        _, status, _ = carbox.solve(N, phi, x0, 0.0, T_END, o, stream=stream, stats=st)
+        x, status, _ = carbox.solve(N, phi, x0, 0.0, T_END, o, stream=stream, stats=st)
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         sd = carbox.stats_dict(st.cpu().numpy())
         lat = (sd["t_end_ns"] - sd["t_begin_ns"]) / 1e6
-        out[name] = {"cells": C, "ms": ms, "value": C / (ms / 1e3), "unit": "cell-solves/s",
+        xs[name] = x[:, :n_err].cpu().numpy()
+        out[name] = {"cells": cells, "ms": ms, "value": cells / (ms / 1e3), "unit": "cell-solves/s",
                      "cells_ok": int((status == 0).sum().item()), "cell_p50_ms": float(np.percentile(lat, 50)),
                      "cell_p99_ms": float(np.percentile(lat, 99)),
-                     "steps_per_cell": float(sd["steps"].mean()), "lu_per_cell": float(sd["lu_factors"].mean())}
+                     "steps_per_cell": float(sd["steps"].mean()), "lu_per_cell": float(sd["lu_factors"].mean()),
+                     "refine_sweeps_per_newton": float(sd["refine_sweeps"].sum() / max(1, sd["newton_iters"].sum()))}
     out["mixed_speedup_vs_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    if errors:
+        ref = oracle_map(net, phi_h[:n_err], x0_h[:, 0], T_END)
+        E = np.vstack([net.composition.T, net.charge[None, :]]).astype(float)
+        e0 = E @ x0_h[:, 0]
+        den = np.where(np.arange(E.shape[0]) == E.shape[0] - 1, np.abs(net.charge) @ x0_h[:, 0], e0)
+        for name in ("mixed", "fp64"):
+            rel, cons = [], 0.0
+            for c in range(n_err):
+                big = ref[:, c] > 1e-12
+                rel.append(np.abs(xs[name][big, c] / ref[big, c] - 1))
+                cons = max(cons, float(np.max(np.abs(E @ xs[name][:, c] - e0) / den)))
+            r = np.concatenate(rel)
+            out[name]["error_vs_fp64_oracle"] = {"cells": n_err, "species_values": int(r.size), "max": float(r.max()),
+                                                 "median": float(np.median(r)), "p99": float(np.percentile(r, 99)),
+                                                 "max_conservation_rel": cons}
     return out
 
 
 def run_large(args):
-    """Config 3: 500 species, mixed vs FP64 throughput and per-species error vs the FP64 oracle."""
+    """Config 3 alone: 500 species, mixed vs FP64 on the same 4,096 cells, errors vs the FP64 oracle."""
     torch, dev, carbox = _gpu_setup()
-    from oracle import bdf, chem
     stream = torch.cuda.current_stream(dev)
-    thr = run_large_throughput(carbox, dev, stream, 4096, 608)
-    net = synth.make_network(500, 6000)
-    N = carbox.Network.from_synth(net)
-    ns = args.ref_cells if args.ref_cells < 64 else 3
-    phi = synth.cells(4096)[:ns]
-    x0 = np.repeat(synth.initial_abundances(net)[:, None], ns, axis=1)
-    errs = {}
-    for name, prec in [("mixed", carbox.CBX_MIXED), ("fp64", carbox.CBX_FP64)]:
-        x, st, _ = carbox.solve_host(N, phi, x0, 0.0, T_END, carbox.options(rtol=RTOL, atol=ATOL, precision=prec))
-        errs[name] = (x, st)
-    rel = {"mixed": [], "fp64": []}
-    cons = {"mixed": 0.0, "fp64": 0.0}
-    E = np.vstack([net.composition.T, net.charge[None, :]]).astype(float)
-    for c in range(ns):
-        ref = bdf.solve_cell(net, phi[c], x0[:, c], 0.0, T_END, RTOL, ATOL)
-        big = ref.x > 1e-12
-        for name in rel:
-            x = errs[name][0][:, c]
-            rel[name].append(np.abs(x[big] / ref.x[big] - 1))
-            e0 = E @ x0[:, c]
-            dE = np.abs(E @ x - e0)
-            den = np.where(np.arange(E.shape[0]) == E.shape[0] - 1, np.abs(net.charge) @ x0[:, c], e0)
-            cons[name] = max(cons[name], float(np.max(dE / den)))
-    res = {"config": "large", "workload": thr["workload"], "throughput": thr, "oracle_cells": ns}
-    for name in rel:
-        r = np.concatenate(rel[name])
-        res["error_vs_fp64_oracle_" + name] = {"max": float(r.max()), "median": float(np.median(r)),
-                                               "p99": float(np.percentile(r, 99)),
-                                               "max_conservation_rel": cons[name]}
-    print(json.dumps(res), flush=True)
+    print(json.dumps({"config": "large", **run_large_throughput(carbox, dev, stream, args.cells if args.cells != 16384
+                                                                else 4096)}), flush=True)
 
 
 def run_adjoint(args):
-    """Config 4: 150 sp, 1024 cells, 1e5 yr; forward (recorded) and adjoint times; gradient checks."""
+    """Config 4 alone, with gradient checks on two cells (oracle adjoint and finite differences)."""
     torch, dev, carbox = _gpu_setup()
+    print(json.dumps(adjoint_block(carbox, dev, torch.cuda.current_stream(dev), checks=2, fd=True)), flush=True)
+
+
+def adjoint_block(carbox, dev, stream, checks=1, fd=False):
+    """Config 4: 150 sp, 1024 cells, 1e5 yr; forward (recorded) and adjoint times;
+    gradient checks on `checks` cells against the oracle adjoint of the GPU's
+    program (and, fd, central finite differences of its exact replay)."""
+    import torch
     from oracle import adjoint as adj
-    from oracle import bdf
-    stream = torch.cuda.current_stream(dev)
     net = synth.make_network(S_SP, R_RX)
     N = carbox.Network.from_synth(net)
     C = 1024
@@ -503,8 +625,9 @@ def run_adjoint(args):
     fwd_ms, bwd_ms = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
     gn_h, gt_h = gn.cpu().numpy(), gt.cpu().numpy()
     # checks on sampled cells: oracle adjoint of the GPU program, and central FD (step 1e-6)
+    cells_checked = [0, 517][:checks]
     checks = []
-    for c in [0, 517]:
+    for c in cells_checked:
         prog = []
         for kind, q, v in tape.program(c):
             prog.append(("init", v) if kind == 0 else ("rescale", q, v) if kind == 1 else ("step", q, v, 0.0, None))
@@ -512,6 +635,11 @@ def run_adjoint(args):
         xr, prog_r = adj.replay(net, phi_h[c], x0_h[:, c], prog)
         _, cr = adj.log10_loss(xr, tg, yt)
         g = adj.adjoint(net, phi_h[c], x0_h[:, c], prog_r, cr)
+        chk = {"cell": c, "rel_err_lnnH_vs_oracle_adjoint": abs(gn_h[c] / g[1] - 1),
+               "rel_err_T_vs_oracle_adjoint": abs(gt_h[c] / g[2] - 1)}
+        checks.append(chk)
+        if not fd:
+            continue
         eps = 1e-6
         pp, pm = phi_h[c].copy(), phi_h[c].copy()
         pp[0] *= np.exp(eps)
@@ -523,26 +651,29 @@ def run_adjoint(args):
         pm[1] -= eps * phi_h[c, 1]
         fd_T = (adj.log10_loss(adj.replay(net, pp, x0_h[:, c], prog)[0], tg, yt)[0] -
                 adj.log10_loss(adj.replay(net, pm, x0_h[:, c], prog)[0], tg, yt)[0]) / (2 * eps * phi_h[c, 1])
-        checks.append({"cell": c, "rel_err_lnnH_vs_oracle_adjoint": abs(gn_h[c] / g[1] - 1),
-                       "rel_err_T_vs_oracle_adjoint": abs(gt_h[c] / g[2] - 1),
-                       "rel_err_lnnH_vs_fd": abs(gn_h[c] / fd_nH - 1), "rel_err_T_vs_fd": abs(gt_h[c] / fd_T - 1)})
+        chk.update({"rel_err_lnnH_vs_fd": abs(gn_h[c] / fd_nH - 1), "rel_err_T_vs_fd": abs(gt_h[c] / fd_T - 1)})
     res = {"config": "adjoint", "workload": f"{S_SP} species / {R_RX} reactions, {C} cells, 0 -> 1e5 yr, FP64, "
                                              "loss = sum over 10 seeded targets of (log10 x - y)^2",
            "forward_record_ms": fwd_ms, "adjoint_ms": bwd_ms, "backward_over_forward": bwd_ms / fwd_ms,
            "cells_ok": int((st == 0).sum().item()), "gradients": "ln alpha [1500] summed over cells, ln n_H [1024], T [1024]",
            "checks": checks}
-    print(json.dumps(res), flush=True)
+    return res
 
 
 def run_zeta(args):
+    """The cosmic-ray sweep alone, with checks on three cells (oracle adjoint and finite differences)."""
+    torch, dev, carbox = _gpu_setup()
+    print(json.dumps(zeta_block(carbox, dev, torch.cuda.current_stream(dev), checks=3, fd=True)), flush=True)
+
+
+def zeta_block(carbox, dev, stream, checks=1, fd=False):
     """Cosmic-ray sweep with sensitivities (synthetic analog of the paper's zeta study,
     Sec. 4 / Fig. 2): 150 sp, the reference cell (n_H 1e4, T 20 K, A_V 5, G0 1) at C
     values of zeta / zeta_0 log-spaced over [1e-2, 1e4], 0 -> 1e7 yr, FP64 forward with
     recording, then the adjoint of L = log10 x_e(t_f) per cell: d log10 x_e / d ln zeta
     (and d/d ln G0, d/dA_V, d/d ln n_H, d/dT) for every cell of the sweep."""
-    torch, dev, carbox = _gpu_setup()
+    import torch
     from oracle import adjoint as adj
-    stream = torch.cuda.current_stream(dev)
     net = synth.make_network(S_SP, R_RX)
     N = carbox.Network.from_synth(net)
     C = 1024
@@ -580,7 +711,7 @@ def run_zeta(args):
     # derivative is zero to rounding, where relative errors mean nothing)
     live = np.flatnonzero(np.abs(gz_h) >= 0.1 * np.abs(gz_h).max())
     checks = []
-    for c in sorted({int(live[0]), int(np.argmax(np.abs(gz_h))), int(live[-1])}):
+    for c in sorted({int(np.argmax(np.abs(gz_h))), int(live[0]), int(live[-1])})[:checks]:
         prog = []
         for kind, q, v in tape.program(c):
             prog.append(("init", v) if kind == 0 else ("rescale", q, v) if kind == 1 else ("step", q, v, 0.0, None))
@@ -589,14 +720,18 @@ def run_zeta(args):
         cr[ie] = 1.0 / (xr[ie] * np.log(10.0))
         g = adj.adjoint(net, phi_h[c], x0_h[:, c], prog_r, cr)
         z_ref = adj.environment_gradients(net, g[0])[0]
+        chk = {"cell": c, "zeta_over_zeta0": float(ratio[c]), "dlog10xe_dlnzeta": float(gz_h[c]),
+               "rel_err_vs_oracle_adjoint": abs(gz_h[c] / z_ref - 1)}
+        checks.append(chk)
+        if not fd:
+            continue
         eps = 1e-6
         pp, pm = phi_h[c].copy(), phi_h[c].copy()
         pp[4] *= np.exp(eps)
         pm[4] *= np.exp(-eps)
         fd = (np.log10(adj.replay(net, pp, x0_h[:, c], prog)[0][ie]) -
               np.log10(adj.replay(net, pm, x0_h[:, c], prog)[0][ie])) / (2 * eps)
-        checks.append({"cell": c, "zeta_over_zeta0": float(ratio[c]), "dlog10xe_dlnzeta": float(gz_h[c]),
-                       "rel_err_vs_oracle_adjoint": abs(gz_h[c] / z_ref - 1), "rel_err_vs_fd": abs(gz_h[c] / fd - 1)})
+        chk["rel_err_vs_fd"] = abs(gz_h[c] / fd - 1)
     ok = st.cpu().numpy() == 0
     grid = [0, C // 4, C // 2, 3 * C // 4, C - 1]
     res = {"config": "zeta", "workload": f"{S_SP} species / {R_RX} reactions, {C} cells, zeta/zeta0 log-spaced in "
@@ -607,17 +742,22 @@ def run_zeta(args):
            "sensitive_range_zeta_over_zeta0": [float(ratio[live[0]]), float(ratio[live[-1]])],
            "dlog10xe_dlnzeta": {f"{ratio[c]:.3g}": float(gz_h[c]) for c in grid},
            "checks": checks}
-    print(json.dumps(res), flush=True)
+    return res
 
 
 def run_track(args):
+    """The time-dependent environment run alone, with two cells checked against the oracle."""
+    torch, dev, carbox = _gpu_setup()
+    print(json.dumps(track_block(carbox, dev, torch.cuda.current_stream(dev), checks=2)), flush=True)
+
+
+def track_block(carbox, dev, stream, checks=1):
     """Time-dependent environment phi(t) (the generalised system of Sec. 2 with phi a function
     of time): 150 sp, 4096 seeded cells, each on a collapse-and-warming track (n_H x10, T x1.5,
     A_V +5 mag over 1 Myr, 4 knots); FP64 and mixed cell-solves/s next to the same cells at
     constant phi, and sampled cells against the oracle's solve_cell_track."""
-    torch, dev, carbox = _gpu_setup()
+    import torch
     from oracle import bdf
-    stream = torch.cuda.current_stream(dev)
     net = synth.make_network(S_SP, R_RX)
     N = carbox.Network.from_synth(net)
     C = 4096
@@ -651,25 +791,30 @@ def run_track(args):
         res[name] = out
         if name == "fp64":
             checks = []
-            for c in [0, 7]:
+            for c in [0, 7][:checks]:
                 ref = bdf.solve_cell_track(net, tr_h[c], x0_h[:, c], 0.0, T_END, RTOL, ATOL).x
                 big = ref > 1e-12
                 checks.append({"cell": c, "max_rel_vs_oracle": float(np.max(np.abs(xt[big, c] / ref[big] - 1)))})
             res["checks_fp64"] = checks
-    print(json.dumps(res), flush=True)
+    return res
 
 
 def run_serving(args):
-    """Config 5: Poisson requests over 32/150/500-species networks through cbx_server."""
+    """Config 5 alone, at the given rate and duration of arrivals."""
     torch, dev, carbox = _gpu_setup()
+    print(json.dumps(serving_block(carbox, args.rate, args.duration)), flush=True)
+
+
+def serving_block(carbox, rate, duration):
+    """Config 5: Poisson requests over 32/150/500-species networks through cbx_server."""
     import threading
     nets = {}
     for S, R in [(32, 200), (150, 1500), (500, 6000)]:
         net = synth.make_network(S, R)
         nets[S] = (net, carbox.Network.from_synth(net))
     rng = np.random.default_rng(13)
-    n_req = max(1, int(rng.poisson(args.rate * args.duration)))
-    arrivals = np.sort(rng.uniform(0.0, args.duration, n_req))
+    n_req = max(1, int(rng.poisson(rate * duration)))
+    arrivals = np.sort(rng.uniform(0.0, duration, n_req))
     reqs = []
     for k in range(n_req):
         S = int(rng.choice([32, 150, 500]))
@@ -709,13 +854,13 @@ def run_serving(args):
         if sel.any():
             by[str(S)] = {"requests": int(sel.sum()), "p50_s": float(np.percentile(lat[sel], 50)),
                           "p99_s": float(np.percentile(lat[sel], 99))}
-    res = {"config": "serving", "workload": f"Poisson arrivals at {args.rate}/s for {args.duration} s; networks "
+    res = {"config": "serving", "workload": f"Poisson arrivals at {rate}/s for {duration} s; networks "
            "32/150/500 species uniform; cells log-uniform 1..4096; spans log-uniform 1e3..1e7 yr; mixed precision",
            "requests": n_req, "cells": cells, "cells_ok": ok, "wall_s": wall,
            "throughput_cells_per_s": cells / wall, "throughput_requests_per_s": n_req / wall,
            "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
            "by_network": by, "server": {"mem_budget": 64 << 30, "streams": 8, "max_ctas": 76, **stats}}
-    print(json.dumps(res), flush=True)
+    return res
 
 
 def main():
@@ -730,7 +875,10 @@ def main():
     ap.add_argument("--only", choices=["fp64", "mixed"], default=None)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-large", action="store_true")
-    ap.add_argument("--config", choices=["bench", "large", "adjoint", "serving", "zeta", "track"], default="bench")
+    ap.add_argument("--no-extras", action="store_true", help="skip the compact config 4/5, track and zeta runs")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the FMA peak probe (nominal peaks)")
+    ap.add_argument("--config", choices=["bench", "large", "adjoint", "serving", "zeta", "track", "peaks"],
+                    default="bench")
     ap.add_argument("--duration", type=float, default=2.0, help="serving: seconds of Poisson arrivals")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean requests per second")
     args = ap.parse_args()
@@ -746,6 +894,11 @@ def main():
         run_zeta(args)
     elif args.config == "track":
         run_track(args)
+    elif args.config == "peaks":
+        torch, dev, carbox = _gpu_setup()
+        with ClockSampler(0) as clk:
+            pk = measure_fma_peaks(carbox, dev, torch.cuda.current_stream(dev))
+        print(json.dumps({"config": "peaks", **(pk or {}), "clocks": clk.summary()}), flush=True)
     else:
         run_gpu(args)
 

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "lib", "libcarbox.so")
 SOURCES = ["solve_fp64.cu", "solve_fp64_gm.cu", "solve_mixed.cu", "solve_mixed_gm.cu", "adjoint.cu", "plan.cu",
-           "network.cpp", "capi.cpp", "noalloc.cu", "server.cpp"]
+           "network.cpp", "capi.cpp", "noalloc.cu", "server.cpp", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -38,7 +38,8 @@ def source_hash() -> str:
     h = hashlib.sha256()
     for f in sorted(SOURCES) + ["internal.h", "solver_dev.cuh"]:
         h.update(open(os.path.join(CSRC, f), "rb").read())
-    h.update(open(os.path.join(INCLUDE, "carbox.h"), "rb").read())
+    for f in sorted(os.listdir(INCLUDE)):
+        h.update(open(os.path.join(INCLUDE, f), "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -115,6 +115,8 @@ def _load():
         "cbx_server_wait": (C.c_int, [P, C.c_uint64, P, P, P]),
         "cbx_server_stats": (C.c_int, [P, C.POINTER(C.c_size_t), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "cbx_server_destroy": (C.c_int, [P]),
+        "cbx_peak_fma": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, P, P]),
+        "cbx_peak_fma_flops": (C.c_double, [C.c_int, C.c_int, C.c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -22,13 +22,13 @@ def declared_symbols():
     for f in os.listdir(os.path.join(ROOT, "include")):
         if f.endswith(".h"):
             txt = open(os.path.join(ROOT, "include", f)).read()
-            names |= set(re.findall(r"^\s*(?:int|const char\*)\s+(cbx_\w+)\s*\(", txt, re.M))
+            names |= set(re.findall(r"^\s*(?:int|double|const char\*)\s+(cbx_\w+)\s*\(", txt, re.M))
     return names
 
 
 def test_exports_every_declared_symbol(lib):
     names = declared_symbols()
-    assert {"cbx_network_create", "cbx_solve", "cbx_solve_host", "cbx_last_error"} <= names
+    assert {"cbx_network_create", "cbx_solve", "cbx_solve_host", "cbx_last_error", "cbx_peak_fma"} <= names
     out = subprocess.run(["nm", "-D", "--defined-only", lib._LIB_PATH], capture_output=True, text=True).stdout
     exported = set(re.findall(r"\bT (cbx_\w+)", out))
     assert names <= exported, names - exported
