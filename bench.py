@@ -450,11 +450,18 @@ def run_gpu(args):
             parity[name] = parity_summary(xs[:, :ncell], x_ref, tight=t_sub)
     extras = None
     if ws == 1 and not args.no_extras:
+        blocks = (("adjoint", lambda: adjoint_block(carbox, dev, stream, n_checks=1)),
+                  ("serving", lambda: serving_block(carbox, rate=200.0, duration=0.25)),
+                  ("track", lambda: track_block(carbox, dev, stream, n_checks=1)),
+                  ("zeta", lambda: zeta_block(carbox, dev, stream, n_checks=1)))
+        extras = {}
         with ClockSampler(local) as clk_x:
-            extras = {"adjoint": adjoint_block(carbox, dev, stream, checks=1),
-                      "serving": serving_block(carbox, rate=200.0, duration=0.25),
-                      "track": track_block(carbox, dev, stream, checks=1),
-                      "zeta": zeta_block(carbox, dev, stream, checks=1)}
+            for name, run in blocks:
+                try:
+                    extras[name] = run()
+                except Exception as exc:  # one failed side run must not lose the headline line
+                    extras[name] = {"error": f"{type(exc).__name__}: {exc}"}
+                    torch.cuda.synchronize(dev)
         extras["clocks"] = clk_x.summary()
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     traffic = None
@@ -578,12 +585,12 @@ def run_large(args):
 def run_adjoint(args):
     """Config 4 alone, with gradient checks on two cells (oracle adjoint and finite differences)."""
     torch, dev, carbox = _gpu_setup()
-    print(json.dumps(adjoint_block(carbox, dev, torch.cuda.current_stream(dev), checks=2, fd=True)), flush=True)
+    print(json.dumps(adjoint_block(carbox, dev, torch.cuda.current_stream(dev), n_checks=2, fd=True)), flush=True)
 
 
-def adjoint_block(carbox, dev, stream, checks=1, fd=False):
+def adjoint_block(carbox, dev, stream, n_checks=1, fd=False):
     """Config 4: 150 sp, 1024 cells, 1e5 yr; forward (recorded) and adjoint times;
-    gradient checks on `checks` cells against the oracle adjoint of the GPU's
+    gradient checks on `n_checks` cells against the oracle adjoint of the GPU's
     program (and, fd, central finite differences of its exact replay)."""
     import torch
     from oracle import adjoint as adj
@@ -625,7 +632,7 @@ def adjoint_block(carbox, dev, stream, checks=1, fd=False):
     fwd_ms, bwd_ms = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
     gn_h, gt_h = gn.cpu().numpy(), gt.cpu().numpy()
     # checks on sampled cells: oracle adjoint of the GPU program, and central FD (step 1e-6)
-    cells_checked = [0, 517][:checks]
+    cells_checked = [0, 517][:n_checks]
     checks = []
     for c in cells_checked:
         prog = []
@@ -663,10 +670,10 @@ def adjoint_block(carbox, dev, stream, checks=1, fd=False):
 def run_zeta(args):
     """The cosmic-ray sweep alone, with checks on three cells (oracle adjoint and finite differences)."""
     torch, dev, carbox = _gpu_setup()
-    print(json.dumps(zeta_block(carbox, dev, torch.cuda.current_stream(dev), checks=3, fd=True)), flush=True)
+    print(json.dumps(zeta_block(carbox, dev, torch.cuda.current_stream(dev), n_checks=3, fd=True)), flush=True)
 
 
-def zeta_block(carbox, dev, stream, checks=1, fd=False):
+def zeta_block(carbox, dev, stream, n_checks=1, fd=False):
     """Cosmic-ray sweep with sensitivities (synthetic analog of the paper's zeta study,
     Sec. 4 / Fig. 2): 150 sp, the reference cell (n_H 1e4, T 20 K, A_V 5, G0 1) at C
     values of zeta / zeta_0 log-spaced over [1e-2, 1e4], 0 -> 1e7 yr, FP64 forward with
@@ -711,7 +718,7 @@ def zeta_block(carbox, dev, stream, checks=1, fd=False):
     # derivative is zero to rounding, where relative errors mean nothing)
     live = np.flatnonzero(np.abs(gz_h) >= 0.1 * np.abs(gz_h).max())
     checks = []
-    for c in sorted({int(np.argmax(np.abs(gz_h))), int(live[0]), int(live[-1])})[:checks]:
+    for c in sorted({int(np.argmax(np.abs(gz_h))), int(live[0]), int(live[-1])})[:n_checks]:
         prog = []
         for kind, q, v in tape.program(c):
             prog.append(("init", v) if kind == 0 else ("rescale", q, v) if kind == 1 else ("step", q, v, 0.0, None))
@@ -748,10 +755,10 @@ def zeta_block(carbox, dev, stream, checks=1, fd=False):
 def run_track(args):
     """The time-dependent environment run alone, with two cells checked against the oracle."""
     torch, dev, carbox = _gpu_setup()
-    print(json.dumps(track_block(carbox, dev, torch.cuda.current_stream(dev), checks=2)), flush=True)
+    print(json.dumps(track_block(carbox, dev, torch.cuda.current_stream(dev), n_checks=2)), flush=True)
 
 
-def track_block(carbox, dev, stream, checks=1):
+def track_block(carbox, dev, stream, n_checks=1):
     """Time-dependent environment phi(t) (the generalised system of Sec. 2 with phi a function
     of time): 150 sp, 4096 seeded cells, each on a collapse-and-warming track (n_H x10, T x1.5,
     A_V +5 mag over 1 Myr, 4 knots); FP64 and mixed cell-solves/s next to the same cells at
@@ -791,7 +798,7 @@ def track_block(carbox, dev, stream, checks=1):
         res[name] = out
         if name == "fp64":
             checks = []
-            for c in [0, 7][:checks]:
+            for c in [0, 7][:n_checks]:
                 ref = bdf.solve_cell_track(net, tr_h[c], x0_h[:, c], 0.0, T_END, RTOL, ATOL).x
                 big = ref > 1e-12
                 checks.append({"cell": c, "max_rel_vs_oracle": float(np.max(np.abs(xt[big, c] / ref[big] - 1)))})
