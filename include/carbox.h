@@ -71,6 +71,11 @@ extern "C" {
                              gamma holds the reaction's cosmic-ray efficiency E and
                              omega is the network's grain albedo (cbx_network_set_albedo) */
 
+/* integration method (cbx_options.method) */
+#define CBX_METHOD_BDF 0     /* variable-order (1..5) BDF, the field's stiff integrator (Sec. 1) */
+#define CBX_METHOD_ESDIRK 1  /* ESDIRK 4(3) of Kvaerno's family, the paper's own kind of solver
+                                (Sec. 4); see cbx_esdirk_tableau */
+
 /* precision of the Newton linear algebra */
 #define CBX_FP64 0   /* LU, triangular solves and everything else in FP64 */
 #define CBX_MIXED 1  /* LU and triangular solves in FP32, FP64 residual r - M dx
@@ -104,7 +109,7 @@ typedef struct {
   int max_steps;      /* step attempts per cell before CBX_CELL_MAX_STEPS (> 0) */
   int precision;      /* CBX_FP64 or CBX_MIXED */
   int max_refine;     /* CBX_MIXED: refinement sweeps per solve (>= 1) */
-  int reserved;
+  int method;         /* CBX_METHOD_BDF (default) or CBX_METHOD_ESDIRK */
   double refine_tol;  /* CBX_MIXED: stop refining when the weighted RMS of the
                          correction is <= refine_tol */
 } cbx_options;
@@ -181,11 +186,30 @@ int cbx_network_info(const cbx_network* net, cbx_netinfo* out);
 int cbx_network_symbolic(const cbx_network* net, int* perm, unsigned char* fill, int* kdense);
 
 /* Default options: rtol 1e-4, atol 1e-20, max_steps 100000, CBX_FP64,
-   max_refine 5, refine_tol 1e-10. */
+   max_refine 5, refine_tol 1e-10, CBX_METHOD_BDF. */
 int cbx_default_options(cbx_options* out);
 
 /*
- * Integrate C cells from t0 to t_end (seconds) with the variable-order BDF.
+ * The Butcher tableau of CBX_METHOD_ESDIRK, for checks (host memory):
+ * a [25] row-major 5 x 5 (lower triangular, a_11 = 0 and a_ii = gamma for
+ * i >= 2), c [5], gamma; any pointer may be NULL. The paper's solver is
+ * Kvaerno's fifth-order ESDIRK (Sec. 4), whose coefficients it does not print;
+ * this is the order-4 member of the same family (Kvaerno, BIT 44, 2004):
+ * explicit first stage, stage order 2, embedded order-3 and order-4
+ * solutions as stages 4 and 5 (both at c = 1), L-stable; the library derives
+ * the coefficients from those conditions (gamma = 0.5728160625).
+ * One step: Y_i = y_n + h sum_{j<i} a_ij f(Y_j) + h gamma f(Y_i) (i = 2..5,
+ * each by simplified Newton with I - h gamma J), y_{n+1} = Y_5, error
+ * estimate Y_5 - Y_4 in the weighted RMS norm, step factor
+ * min(10, max(0.2, 0.9 err^(-1/4))).
+ */
+int cbx_esdirk_tableau(double* a, double* c, double* gamma);
+
+/*
+ * Integrate C cells from t0 to t_end (seconds) with the variable-order BDF
+ * (or the ESDIRK of cbx_esdirk_tableau when opt->method is CBX_METHOD_ESDIRK;
+ * that method supports networks whose Newton matrix fits in shared memory,
+ * S <= 256, and has no adjoint: recording entry points reject it).
  *   phi    [C]     device pointer, cell parameters (Sec. 2: k(phi)).
  *   x0     [S][C]  device pointer, initial abundances per n_H.
  *   opt            host pointer (NULL = defaults).

@@ -213,3 +213,21 @@ def solve_cell(net, phi, x0, t0, t_end, rtol, atol, max_steps=100000):
     return integrate(lambda t, y: chem.rhs(net, kappa, y, nu),
                      lambda t, y: chem.jacobian(net, kappa, y, nu),
                      t0, np.asarray(x0, dtype=float), t_end, rtol, atol, max_steps)
+
+
+def solve_cell_track(net, track, x0, t0, t_end, rtol, atol, max_steps=100000):
+    """Integrate one cell whose environment follows `track` (see
+    bdf.solve_cell_track): the coefficients are those of phi(t) at every time
+    at which the method evaluates f or J."""
+    nu = chem.stoichiometry(net)
+    last = {}
+
+    def kappa(t):
+        if last.get("t") != t:
+            last["t"] = t
+            last["k"] = chem.effective_coefficients(net, bdf.track_params(track, t))
+        return last["k"]
+
+    return integrate(lambda t, y: chem.rhs(net, kappa(t), y, nu),
+                     lambda t, y: chem.jacobian(net, kappa(t), y, nu),
+                     t0, np.asarray(x0, dtype=float), t_end, rtol, atol, max_steps)

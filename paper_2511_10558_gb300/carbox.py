@@ -20,6 +20,7 @@ CBX_CELL_OK, CBX_CELL_MAX_STEPS, CBX_CELL_H_UNDERFLOW, CBX_CELL_BAD_INPUT = 0, 1
 CBX_CELL_TAPE_FULL = 6
 CBX_TWO_BODY, CBX_COSMIC_RAY, CBX_PHOTO, CBX_CR_PHOTO = 0, 1, 2, 3
 CBX_FP64, CBX_MIXED = 0, 1
+CBX_METHOD_BDF, CBX_METHOD_ESDIRK = 0, 1
 
 
 class cbx_species(C.Structure):
@@ -38,7 +39,7 @@ class cbx_cell_params(C.Structure):
 
 class cbx_options(C.Structure):
     _fields_ = [("rtol", C.c_double), ("atol", C.c_double), ("max_steps", C.c_int), ("precision", C.c_int),
-                ("max_refine", C.c_int), ("reserved", C.c_int), ("refine_tol", C.c_double)]
+                ("max_refine", C.c_int), ("method", C.c_int), ("refine_tol", C.c_double)]
 
 
 class cbx_cell_stats(C.Structure):
@@ -116,6 +117,7 @@ def _load():
         "cbx_server_stats": (C.c_int, [P, C.POINTER(C.c_size_t), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "cbx_server_destroy": (C.c_int, [P]),
         "cbx_peak_fma": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, P, P]),
+        "cbx_esdirk_tableau": (C.c_int, [P, P, C.POINTER(C.c_double)]),
         "cbx_peak_fma_flops": (C.c_double, [C.c_int, C.c_int, C.c_int]),
     }
     for name, (res, args) in sig.items():
@@ -139,12 +141,23 @@ def check(code, where):
         raise CarboxError(code, where)
 
 
-def options(rtol=1e-4, atol=1e-20, max_steps=100000, precision=CBX_FP64, max_refine=5, refine_tol=1e-10):
+def options(rtol=1e-4, atol=1e-20, max_steps=100000, precision=CBX_FP64, max_refine=5, refine_tol=1e-10,
+            method=CBX_METHOD_BDF):
     o = cbx_options()
     check(lib.cbx_default_options(C.byref(o)), "cbx_default_options")
     o.rtol, o.atol, o.max_steps, o.precision = rtol, atol, max_steps, precision
-    o.max_refine, o.refine_tol = max_refine, refine_tol
+    o.max_refine, o.refine_tol, o.method = max_refine, refine_tol, method
     return o
+
+
+def esdirk_tableau():
+    """(A [5, 5], c [5], gamma) of CBX_METHOD_ESDIRK as the library derived it."""
+    a = np.zeros(25)
+    c = np.zeros(5)
+    g = C.c_double()
+    check(lib.cbx_esdirk_tableau(a.ctypes.data_as(C.c_void_p), c.ctypes.data_as(C.c_void_p), C.byref(g)),
+          "cbx_esdirk_tableau")
+    return a.reshape(5, 5), c, g.value
 
 
 class Network:

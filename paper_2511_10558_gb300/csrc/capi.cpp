@@ -47,6 +47,8 @@ int check_options(const cbx_options& o) {
   if (o.precision != CBX_FP64 && o.precision != CBX_MIXED) return fail(CBX_E_ARG, "precision must be CBX_FP64 or CBX_MIXED");
   if (o.precision == CBX_MIXED && o.max_refine < 1) return fail(CBX_E_ARG, "max_refine must be >= 1");
   if (!(o.refine_tol >= 0.0)) return fail(CBX_E_ARG, "refine_tol must be >= 0");
+  if (o.method != CBX_METHOD_BDF && o.method != CBX_METHOD_ESDIRK)
+    return fail(CBX_E_ARG, "method must be CBX_METHOD_BDF or CBX_METHOD_ESDIRK");
   return CBX_OK;
 }
 
@@ -153,6 +155,7 @@ int cbx_default_options(cbx_options* out) {
   out->precision = CBX_FP64;
   out->max_refine = 5;
   out->refine_tol = 1e-10;
+  out->method = CBX_METHOD_BDF;
   return CBX_OK;
 }
 
@@ -235,6 +238,8 @@ static int solve_impl(cbx_network* net, const cbx_cell_params* phi, const double
   if (opt) o = *opt;
   int rc = check_options(o);
   if (rc) return rc;
+  const bool rk = o.method == CBX_METHOD_ESDIRK;
+  if (rk && tape) return fail(CBX_E_ARG, "recording (the adjoint) is implemented for CBX_METHOD_BDF only");
   if (C == 0) return CBX_OK;
   rc = upload(net);
   if (rc) return rc;
@@ -248,6 +253,8 @@ static int solve_impl(cbx_network* net, const cbx_cell_params* phi, const double
              h.S, h.R, plan.smem, 512, device_smem_optin());
     return fail(CBX_E_TOO_LARGE, m);
   }
+  if (rk && plan.gm)
+    return fail(CBX_E_TOO_LARGE, "CBX_METHOD_ESDIRK supports networks whose Newton matrix fits in shared memory");
   int grid = std::min(C, occ * device_sm_count());
   if (max_grid > 0) grid = std::min(grid, max_grid);
   cudaStream_t st = (cudaStream_t)stream;
@@ -283,8 +290,16 @@ static int solve_impl(cbx_network* net, const cbx_cell_params* phi, const double
   if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(workspace)");
   a.ws = (double*)ws;
   a.counter = (int*)((char*)ws + (size_t)grid * a.ws_stride * sizeof(double));
+  if (rk) {
+    const EsdirkTableau& tb = esdirk_tableau();
+    for (int i = 0; i < 5; ++i) {
+      a.rk_c[i] = tb.c[i];
+      for (int j = 0; j < 5; ++j) a.rk_a[i][j] = tb.a[i][j];
+    }
+  }
   e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
-  if (e == cudaSuccess) e = (cudaError_t)launch_solver(a, plan, grid, stream);
+  if (e == cudaSuccess)
+    e = (cudaError_t)(rk ? launch_solver_rk(a, plan, grid, stream) : launch_solver(a, plan, grid, stream));
   cudaError_t e2 = cudaFreeAsync(ws, st);
   if (e != cudaSuccess) return cuda_fail(e, "solver launch");
   if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync(workspace)");

@@ -113,7 +113,20 @@ struct SolveArgs {
   int piv_ints;    // pivot-list ints staged in shared memory (set by launch_solver)
   const double* track;  // [C][K][6] (t, n_H, T, A_V, G0, zeta) knots, or null: phi is constant
   int K;
+  // ESDIRK tableau (CBX_METHOD_ESDIRK): A [5][5] lower triangular, c [5], gamma = A[i][i], i >= 1
+  double rk_a[5][5];
+  double rk_c[5];
 };
+
+// The ESDIRK 4(3) of Kvaerno's family (explicit first stage, stage order 2,
+// embedded and final solutions as stages 4 and 5, L-stable), derived on the
+// host from those conditions; computed once.
+struct EsdirkTableau {
+  double a[5][5];
+  double c[5];
+  double gamma;
+};
+const EsdirkTableau& esdirk_tableau();
 
 struct GradArgs {
   DevNet net;
@@ -168,6 +181,10 @@ int occupancy_solve_fp64(size_t smem);
 int occupancy_solve_fp64_gm(size_t smem);
 int occupancy_solve_mixed(size_t smem);
 int occupancy_solve_mixed_gm(size_t smem);
+int launch_solve_fp64_rk(const SolveArgs& a, size_t smem, int grid, void* stream);
+int launch_solve_mixed_rk(const SolveArgs& a, size_t smem, int grid, void* stream);
+// Launch the ESDIRK solver (shared-memory matrix only); returns a cudaError_t value.
+int launch_solver_rk(const SolveArgs& a, const SolverPlan& p, int grid, void* stream);
 int device_sm_count();
 // cbx_solve on device buffers with at most max_grid CTAs (0: no cap).
 int solve_device(cbx_network* net, const cbx_cell_params* phi, const double* x0, int C, double t0, double t_end,

@@ -92,6 +92,7 @@ extern "C" int cbx_solve_noalloc(cbx_network* net, const cbx_cell_params* phi, c
       (o.precision != CBX_FP64 && o.precision != CBX_MIXED) || (o.precision == CBX_MIXED && o.max_refine < 1) ||
       !(o.refine_tol >= 0.0))
     return fail(CBX_E_ARG, "invalid options (see cbx_options in carbox.h)");
+  if (o.method != CBX_METHOD_BDF) return fail(CBX_E_ARG, "cbx_solve_noalloc runs CBX_METHOD_BDF only");
   if (C == 0) return CBX_OK;
   if (!net->dbuf) return fail(CBX_E_ARG, "network tables are not on a device: create the network with a GPU present");
   int dev = 0;

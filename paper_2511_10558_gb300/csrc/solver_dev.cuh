@@ -1170,9 +1170,9 @@ __device__ cbx_cell_params track_params(const double* track, int K, int cell, do
 }
 
 // Every knot finite with n_H, T > 0, and the knot times strictly increasing.
-__device__ bool track_valid(const SolveArgs& a, int cell) {
-  const double* k0 = a.track + (size_t)cell * a.K * 6;
-  for (int k = 0; k < a.K; ++k) {
+__device__ bool track_valid(const double* track, int K, int cell) {
+  const double* k0 = track + (size_t)cell * K * 6;
+  for (int k = 0; k < K; ++k) {
     const double* A = k0 + k * 6;
     for (int f = 0; f < 6; ++f)
       if (!isfinite(A[f])) return false;
@@ -1201,7 +1201,7 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
   rec.on = a.tape.nops != nullptr;
   for (int i = threadIdx.x; i < S; i += NT) s.y[i] = a.x0[(size_t)__ldg(n.perm + i) * a.C + cell];
   if (!(p.n_H > 0.0) || !(p.T > 0.0) || !isfinite(p.n_H) || !isfinite(p.T) || !isfinite(p.A_V) ||
-      !isfinite(p.G0) || !isfinite(p.zeta) || (a.track && !track_valid(a, cell))) {
+      !isfinite(p.G0) || !isfinite(p.zeta) || (a.track && !track_valid(a.track, a.K, cell))) {
     status = CBX_CELL_BAD_INPUT;
     __syncthreads();
     for (int i = threadIdx.x; i < S; i += NT) a.x_out[(size_t)__ldg(n.perm + i) * a.C + cell] = s.y[i];
@@ -1368,7 +1368,188 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
   }
   __syncthreads();
 }
+// ---------------------------------------------------------------- ESDIRK
+//
+// The stiff integrator of the paper's own code is an ESDIRK of Kvaerno's
+// family (Sec. 4). One step of size h from (t_n, y_n), with f_1 = f(t_n, y_n)
+// (the previous step's f_5):
+//   stage i = 2..5:  Y_i = y_n + h sum_{j<i} a_ij f_j + h gamma f(t_n + c_i h, Y_i)
+//   y_{n+1} = Y_5, embedded Y_4 (both at c = 1), error estimate Y_5 - Y_4.
+// Each stage is the corrector d - hgamma f(Y_{i-1} + d) + (Y_{i-1} - known) = 0
+// solved by the same simplified Newton as the BDF (guess Y_{i-1}, matrix
+// I - h gamma J, one LU for the four stages). Controller: err = |Y_5 - Y_4|
+// (weights from |Y_5|) <= 1; h *= min(10, max(0.2, 0.9 err^(-1/4))) after an
+// accepted step, max(0.2, 0.9 err^(-1/4)) after a rejected one; Newton
+// failure: new J at (t_n, y_n) if stale, else h / 2; J at the start and after
+// such failures; LU whenever h or J changed; initial step of Hairer, Norsett &
+// Wanner I, II.4 with p = 3; last step shortened to t_end.
+// Shared memory: the stage derivatives f_1..f_5 take rows 0..4 of the BDF's
+// difference array, y_n row 5, the previous stage value row 6.
 template <typename LT, bool GM>
+__device__ void solve_cell_rk(const SolveArgs& a, int cell, Smem& s, double* ws) {
+  const DevNet& n = a.net;
+  const int S = n.S;
+  LT* M = GM ? (LT*)(ws + (3LL * n.R + n.nnzJ + 31) / 32 * 32) : (LT*)s.M;
+  __shared__ cbx_cell_stats s_stats;
+  Cell<LT, GM> c{a, n, s, M, ws, ws + n.R, ws + 3 * n.R, &s_stats};
+  if (threadIdx.x == 0) {
+    *c.st = cbx_cell_stats{};
+    c.st->t_begin_ns = (long long)globaltimer();
+  }
+  int attempts = 0;
+  const cbx_cell_params p = a.track ? track_params(a.track, a.K, cell, a.t0) : a.phi[cell];
+  int status = CBX_CELL_OK;
+  double* F = s.D;           // f_1..f_5, rows 0..4
+  double* yn = s.D + 5 * S;  // y_n
+  double* yprev = s.D + 6 * S;
+  for (int i = threadIdx.x; i < S; i += NT) yn[i] = a.x0[(size_t)__ldg(n.perm + i) * a.C + cell];
+  if (!(p.n_H > 0.0) || !(p.T > 0.0) || !isfinite(p.n_H) || !isfinite(p.T) || !isfinite(p.A_V) ||
+      !isfinite(p.G0) || !isfinite(p.zeta) || (a.track && !track_valid(a.track, a.K, cell))) {
+    status = CBX_CELL_BAD_INPUT;
+    __syncthreads();
+    for (int i = threadIdx.x; i < S; i += NT) a.x_out[(size_t)__ldg(n.perm + i) * a.C + cell] = yn[i];
+  } else {
+    rate_coefficients(n, a.alpha, p, c.kap);
+    __syncthreads();
+    double t_rates = a.t0;
+    auto rates_at = [&](double tt) {
+      if (a.track && tt != t_rates) {
+        rate_coefficients(n, a.alpha, track_params(a.track, a.K, cell, tt), c.kap);
+        __syncthreads();
+        t_rates = tt;
+      }
+    };
+    const double rtol = a.rtol, atol = a.atol, t_end = a.t_end;
+    const double gamma = a.rk_a[1][1];
+    double* slot = s.red + 40;
+    // f_1 and the initial step (Hairer, Norsett & Wanner I, II.4, p = 3)
+    rhs(n, c.kap, yn, F, s.r, s.part);
+    if (threadIdx.x == 0) c.st->rhs_evals++;
+    for (int i = threadIdx.x; i < S; i += NT) s.wsc[i] = 1.0 / (atol + rtol * fabs(yn[i]));
+    __syncthreads();
+    const double d0 = wrms(yn, s.wsc, 1.0, S, s.red);
+    const double d1 = wrms(F, s.wsc, 1.0, S, s.red);
+    const double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
+    for (int i = threadIdx.x; i < S; i += NT) s.tmp[i] = yn[i] + h0 * F[i];
+    __syncthreads();
+    rates_at(a.t0 + h0);
+    rhs(n, c.kap, s.tmp, s.dy, s.r, s.part);
+    if (threadIdx.x == 0) c.st->rhs_evals++;
+    for (int i = threadIdx.x; i < S; i += NT) s.tmp[i] = s.dy[i] - F[i];
+    __syncthreads();
+    const double d2 = wrms(s.tmp, s.wsc, 1.0, S, s.red) / h0;
+    const double dm = fmax(d1, d2);
+    const double h1 = dm <= 1e-15 ? fmax(1e-6, h0 * 1e-3) : uniform_pow(0.01 / dm, 0.25, slot);
+    double t = a.t0;
+    double h = fmin(fmin(100.0 * h0, h1), t_end - t);
+    rates_at(a.t0);
+    jacobian(n, c.kap, yn, c.g, c.Jv);
+    if (threadIdx.x == 0) c.st->jac_evals++;
+    bool jac_current = true, lu_valid = false;
+    double lu_h = 0.0, err = 0.0;
+    while (t < t_end) {
+      bool accepted = false;
+      while (!accepted) {
+        if (attempts >= a.max_steps) {
+          status = CBX_CELL_MAX_STEPS;
+          break;
+        }
+        attempts++;
+        if (h < 10.0 * (::nextafter(t, __longlong_as_double(0x7ff0000000000000LL)) - t)) {
+          status = CBX_CELL_H_UNDERFLOW;
+          break;
+        }
+        if (t + h > t_end) h = t_end - t;
+        const double hg = h * gamma;
+        bool failed;
+        for (;;) {
+          if (!lu_valid || lu_h != h) {
+            factor(c, hg);
+            lu_valid = true;
+            lu_h = h;
+          }
+          failed = false;
+          for (int i = threadIdx.x; i < S; i += NT) {
+            yprev[i] = yn[i];
+            s.wsc[i] = 1.0 / (atol + rtol * fabs(yn[i]));
+          }
+          __syncthreads();
+          for (int st = 1; st < 5; ++st) {
+            const double ti = t + a.rk_c[st] * h;
+            // guess Y_{i-1}; psi = guess - known, known = y_n + h sum_{j<i} a_ij f_j
+            for (int i = threadIdx.x; i < S; i += NT) {
+              double known = 0.0;
+              for (int j = 0; j < st; ++j) known = fma(a.rk_a[st][j], F[j * S + i], known);
+              known = fma(h, known, yn[i]);
+              s.yp[i] = yprev[i];
+              s.psi[i] = yprev[i] - known;
+            }
+            __syncthreads();
+            rates_at(ti);
+            int iters = 0;
+            const bool conv = newton(c, hg, &iters);
+            if (threadIdx.x == 0) c.st->newton_iters += iters;
+            if (!conv) {
+              failed = true;
+              break;
+            }
+            rhs(n, c.kap, s.y, F + st * S, s.r, s.part);
+            if (threadIdx.x == 0) c.st->rhs_evals++;
+            if (st < 4) {  // after the last stage yprev keeps the embedded solution Y_4
+              for (int i = threadIdx.x; i < S; i += NT) yprev[i] = s.y[i];
+              __syncthreads();
+            }
+          }
+          if (!failed || jac_current) break;
+          rates_at(t);
+          jacobian(n, c.kap, yn, c.g, c.Jv);
+          if (threadIdx.x == 0) c.st->jac_evals++;
+          jac_current = true;
+          lu_valid = false;
+        }
+        if (failed) {
+          if (threadIdx.x == 0) c.st->newton_fails++;
+          h *= 0.5;
+          continue;
+        }
+        // error estimate Y_5 - Y_4 (s.y = Y_5, yprev = Y_4), weights from |Y_5|
+        for (int i = threadIdx.x; i < S; i += NT) {
+          s.wsc[i] = 1.0 / (atol + rtol * fabs(s.y[i]));
+          s.tmp[i] = s.y[i] - yprev[i];
+        }
+        __syncthreads();
+        err = wrms(s.tmp, s.wsc, 1.0, S, s.red);
+        if (err > 1.0) {
+          if (threadIdx.x == 0) c.st->error_fails++;
+          h *= fmax(0.2, 0.9 * uniform_pow(err, -0.25, slot));
+          continue;
+        }
+        accepted = true;
+      }
+      if (!accepted) break;
+      if (threadIdx.x == 0) c.st->steps++;
+      t = t + h;
+      for (int i = threadIdx.x; i < S; i += NT) {
+        yn[i] = s.y[i];
+        F[i] = F[4 * S + i];
+      }
+      __syncthreads();
+      jac_current = false;
+      const double fac = err == 0.0 ? 10.0 : 0.9 * uniform_pow(err, -0.25, slot);
+      h *= fmin(10.0, fmax(0.2, fac));
+    }
+    for (int i = threadIdx.x; i < S; i += NT) a.x_out[(size_t)__ldg(n.perm + i) * a.C + cell] = yn[i];
+  }
+  if (threadIdx.x == 0) {
+    a.status[cell] = status;
+    c.st->attempts = attempts;
+    c.st->t_end_ns = (long long)globaltimer();
+    if (a.stats) a.stats[cell] = *c.st;
+  }
+  __syncthreads();
+}
+
+template <typename LT, bool GM, bool RK = false>
 __global__ void __launch_bounds__(NT, 1) solve_kernel(const SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_cell;
@@ -1385,15 +1566,18 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(const SolveArgs a) {
     const int cell = s_cell;
     __syncthreads();
     if (cell >= a.C) break;
-    solve_cell<LT, GM>(a, cell, s, ws);
+    if constexpr (RK)
+      solve_cell_rk<LT, GM>(a, cell, s, ws);
+    else
+      solve_cell<LT, GM>(a, cell, s, ws);
   }
 }
 
-template <typename LT, bool GM>
+template <typename LT, bool GM, bool RK = false>
 static int launch_t(const SolveArgs& a, size_t sm, int grid, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(solve_kernel<LT, GM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = cudaFuncSetAttribute(solve_kernel<LT, GM, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  solve_kernel<LT, GM><<<grid, NT, sm, st>>>(a);
+  solve_kernel<LT, GM, RK><<<grid, NT, sm, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -26,18 +26,20 @@ TIGHT = (1e-8, 1e-26)
 
 
 def _worker(args):
-    net, phi, x0, t_end, rtol, atol, track = args
-    from oracle import bdf
+    net, phi, x0, t_end, rtol, atol, track, method = args
+    from oracle import bdf, esdirk
+    mod = esdirk if method == "esdirk" else bdf
     if track is None:
-        return bdf.solve_cell(net, phi, x0, 0.0, t_end, rtol, atol).x
-    return bdf.solve_cell_track(net, track, x0, 0.0, t_end, rtol, atol).x
+        return mod.solve_cell(net, phi, x0, 0.0, t_end, rtol, atol).x
+    return mod.solve_cell_track(net, track, x0, 0.0, t_end, rtol, atol).x
 
 
-def oracle_cells(net, phis, x0s, t_end, rtol=1e-4, atol=1e-20, tracks=None):
-    """Oracle results [S, n] for cells phis[i] (or tracks[i]) with x0s[:, i]."""
+def oracle_cells(net, phis, x0s, t_end, rtol=1e-4, atol=1e-20, tracks=None, method="bdf"):
+    """Oracle results [S, n] for cells phis[i] (or tracks[i]) with x0s[:, i],
+    by the BDF (method "bdf") or the ESDIRK ("esdirk") oracle."""
     n = len(phis) if tracks is None else len(tracks)
     jobs = [(net, None if tracks is not None else np.asarray(phis[i]), np.asarray(x0s[:, i]), t_end, rtol, atol,
-             None if tracks is None else np.asarray(tracks[i])) for i in range(n)]
+             None if tracks is None else np.asarray(tracks[i]), method) for i in range(n)]
     old = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS")}
     os.environ["OPENBLAS_NUM_THREADS"] = os.environ["OMP_NUM_THREADS"] = "1"
     try:

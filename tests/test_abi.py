@@ -142,3 +142,19 @@ def test_set_albedo_checks(lib):
     for bad in (1.0, -0.1, float("nan"), 2.0):
         assert lib.lib.cbx_network_set_albedo(N.handle, C.c_double(bad)) == lib.CBX_E_ARG
     assert lib.lib.cbx_network_set_albedo(None, C.c_double(0.3)) == lib.CBX_E_ARG
+
+
+def test_esdirk_tableau_of_the_library(lib):
+    # the library derives the ESDIRK tableau on its own (C++); it must satisfy
+    # the order conditions and match the oracle's independent derivation
+    from oracle import esdirk
+    A, c, gamma = lib.esdirk_tableau()
+    b, bh = A[4], A[3]
+    Ac = A @ c
+    for v, want in ((b.sum(), 1), (b @ c, 1 / 2), (b @ c ** 2, 1 / 3), (b @ Ac, 1 / 6), (b @ c ** 3, 1 / 4),
+                    (b @ (c * Ac), 1 / 8), (b @ (A @ c ** 2), 1 / 12), (b @ (A @ Ac), 1 / 24),
+                    (bh.sum(), 1), (bh @ c, 1 / 2), (bh @ c ** 2, 1 / 3), (bh @ Ac, 1 / 6)):
+        assert abs(v - want) < 1e-14
+    assert gamma == pytest.approx(0.5728160625, abs=1e-9)
+    np.testing.assert_allclose(A, esdirk.A_TAB, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(c, esdirk.C_TAB, rtol=0, atol=1e-14)
