@@ -375,21 +375,31 @@ int cbx_tape_program(const cbx_tape* tape, int cell, int* kinds, int* qs, double
 /*
  * Continuous-batching request server (serving many 0-D cell solves of the
  * Sec. 2 ODE for different networks). A scheduler thread admits submitted
- * requests, in arrival order with smaller ones allowed past a head that does
- * not fit, whenever one of `n_streams` CUDA streams and enough of the device
- * memory budget `mem_budget` (bytes: inputs, outputs and solver workspace of
- * the request) are free. Admitted requests run concurrently: each uses at most
- * `max_ctas` persistent CTAs (0 = the whole device), which keep a cell's solver
- * state on chip, retire it and back-fill from the request's remaining cells.
- * Results are bitwise the same whatever else is in flight.
+ * requests in arrival order whenever one of `n_streams` CUDA streams and
+ * enough of the device-memory budget (inputs, outputs and solver workspace)
+ * are free; a request that does not fit may be passed by later, smaller ones
+ * at most 8 times, after which nothing else is admitted before it. Queued
+ * requests for the same network with the same options and t0 are merged into
+ * one launch (up to 65,536 cells), each keeping its own t_end, so that the
+ * launch's persistent CTAs back-fill across requests. Admitted launches run
+ * concurrently, each with at most `max_ctas` CTAs (0 = the whole device); a
+ * cell's solver state stays on chip for its whole solve. Results are bitwise
+ * the same whatever else is in flight or merged.
+ *   mem_budget: 0 = 80 % of the device memory free at creation; otherwise a
+ *               cap, itself limited to that figure.
  * Host arrays are copied at submit (phi [C], x0 [S][C]); cbx_server_wait
  * blocks until the request is done and copies x_out [S][C] and cell_status [C]
  * out (either may be NULL); times (3 doubles, may be NULL) receive the submit,
  * start and completion times in seconds of a steady clock. A request's id is
  * released by cbx_server_wait. cbx_server_poll gives its state (0 queued,
  * 1 running, 2 done, 3 failed) and, when finished, its latency in seconds.
- * cbx_server_destroy waits for running requests and drops queued ones.
- * Errors: CBX_E_ARG, CBX_E_TOO_LARGE (request above the budget), CBX_E_CUDA.
+ * cbx_server_info gives the budget in use, the number of launches and how
+ * many requests were merged into another's launch.
+ * cbx_server_destroy fails the queued requests (their cbx_server_wait returns
+ * CBX_E_ARG), waits for the running ones and for every thread blocked in
+ * cbx_server_wait, then frees the server; no call may use it afterwards.
+ * Errors: CBX_E_ARG, CBX_E_TOO_LARGE (request above the budget or above
+ * 65,536 cells), CBX_E_CUDA.
  */
 int cbx_server_create(size_t mem_budget, int n_streams, int max_ctas, cbx_server** out);
 int cbx_server_submit(cbx_server* server, cbx_network* net, const cbx_cell_params* phi, const double* x0, int C,
@@ -397,6 +407,7 @@ int cbx_server_submit(cbx_server* server, cbx_network* net, const cbx_cell_param
 int cbx_server_poll(cbx_server* server, uint64_t request_id, int* state, double* latency_s);
 int cbx_server_wait(cbx_server* server, uint64_t request_id, double* x_out, int* cell_status, double* times);
 int cbx_server_stats(cbx_server* server, size_t* peak_bytes, int* peak_running, int* queued);
+int cbx_server_info(cbx_server* server, size_t* budget, long long* launches, long long* merged_requests);
 int cbx_server_destroy(cbx_server* server);
 
 /*

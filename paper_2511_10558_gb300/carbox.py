@@ -116,6 +116,7 @@ def _load():
         "cbx_server_wait": (C.c_int, [P, C.c_uint64, P, P, P]),
         "cbx_server_stats": (C.c_int, [P, C.POINTER(C.c_size_t), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "cbx_server_destroy": (C.c_int, [P]),
+        "cbx_server_info": (C.c_int, [P, C.POINTER(C.c_size_t), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
         "cbx_peak_fma": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, P, P]),
         "cbx_esdirk_tableau": (C.c_int, [P, P, C.POINTER(C.c_double)]),
         "cbx_peak_fma_flops": (C.c_double, [C.c_int, C.c_int, C.c_int]),
@@ -473,7 +474,7 @@ def cell_solve(log_alpha, log_nH, T, net, x0, av_g0_zeta, t_end, opt=None, max_s
 class Server:
     """cbx_server: continuous-batching solves of host-side requests."""
 
-    def __init__(self, mem_budget=8 << 30, n_streams=8, max_ctas=76):
+    def __init__(self, mem_budget=0, n_streams=8, max_ctas=76):
         h = C.c_void_p()
         check(lib.cbx_server_create(int(mem_budget), int(n_streams), int(max_ctas), C.byref(h)), "cbx_server_create")
         self.handle = h
@@ -513,6 +514,13 @@ class Server:
         q = C.c_int()
         check(lib.cbx_server_stats(self.handle, C.byref(b), C.byref(r), C.byref(q)), "cbx_server_stats")
         return {"peak_bytes": b.value, "peak_running": r.value, "queued": q.value}
+
+    def info(self):
+        b = C.c_size_t()
+        n = C.c_longlong()
+        m = C.c_longlong()
+        check(lib.cbx_server_info(self.handle, C.byref(b), C.byref(n), C.byref(m)), "cbx_server_info")
+        return {"budget": b.value, "launches": n.value, "merged_requests": m.value}
 
     def close(self):
         if self.handle:

@@ -136,8 +136,6 @@ struct cbx_tape {
 namespace cbx {
 // Record an error message for cbx_last_error() from another translation unit.
 int record_error(int code, const std::string& msg) { return fail(code, msg); }
-int solve_device(cbx_network* net, const cbx_cell_params* phi, const double* x0, int C, double t0, double t_end,
-                 const cbx_options* opt, void* stream, double* x_out, int* cell_status, int max_grid);
 }  // namespace cbx
 
 extern "C" {
@@ -228,7 +226,7 @@ int cbx_network_symbolic(const cbx_network* net, int* perm, unsigned char* fill,
 static int solve_impl(cbx_network* net, const cbx_cell_params* phi, const double* x0, int C, double t0,
                       double t_end, const cbx_options* opt, void* stream, double* x_out, int* cell_status,
                       cbx_cell_stats* stats, cbx_tape* tape, int max_grid = 0, const double* track = nullptr,
-                      int K = 0, const double* alpha = nullptr) {
+                      int K = 0, const double* alpha = nullptr, const double* t_end_cell = nullptr) {
   if (!net) return fail(CBX_E_ARG, "net is NULL");
   if (C < 0) return fail(CBX_E_ARG, "C must be >= 0");
   if (C > 0 && ((!phi && !track) || !x0 || !x_out || !cell_status)) return fail(CBX_E_ARG, "NULL array with C > 0");
@@ -264,6 +262,7 @@ static int solve_impl(cbx_network* net, const cbx_cell_params* phi, const double
   a.phi = phi;
   a.track = track;
   a.K = K;
+  a.t_end_cell = t_end_cell;
   a.x0 = x0;
   a.C = C;
   a.t0 = t0;
@@ -598,7 +597,9 @@ int cbx_tape_program(const cbx_tape* tape, int cell, int* kinds, int* qs, double
 
 namespace cbx {
 int solve_device(cbx_network* net, const cbx_cell_params* phi, const double* x0, int C, double t0, double t_end,
-                 const cbx_options* opt, void* stream, double* x_out, int* cell_status, int max_grid) {
-  return solve_impl(net, phi, x0, C, t0, t_end, opt, stream, x_out, cell_status, nullptr, nullptr, max_grid);
+                 const cbx_options* opt, void* stream, double* x_out, int* cell_status, int max_grid,
+                 const double* t_end_cell) {
+  return solve_impl(net, phi, x0, C, t0, t_end, opt, stream, x_out, cell_status, nullptr, nullptr, max_grid, nullptr,
+                    0, nullptr, t_end_cell);
 }
 }  // namespace cbx

@@ -113,6 +113,7 @@ struct SolveArgs {
   int piv_ints;    // pivot-list ints staged in shared memory (set by launch_solver)
   const double* track;  // [C][K][6] (t, n_H, T, A_V, G0, zeta) knots, or null: phi is constant
   int K;
+  const double* t_end_cell;  // [C] per-cell end times (device), or null: t_end for every cell
   // ESDIRK tableau (CBX_METHOD_ESDIRK): A [5][5] lower triangular, c [5], gamma = A[i][i], i >= 1
   double rk_a[5][5];
   double rk_c[5];
@@ -186,9 +187,12 @@ int launch_solve_mixed_rk(const SolveArgs& a, size_t smem, int grid, void* strea
 // Launch the ESDIRK solver (shared-memory matrix only); returns a cudaError_t value.
 int launch_solver_rk(const SolveArgs& a, const SolverPlan& p, int grid, void* stream);
 int device_sm_count();
-// cbx_solve on device buffers with at most max_grid CTAs (0: no cap).
+// cbx_solve on device buffers with at most max_grid CTAs (0: no cap) and,
+// optionally, per-cell end times t_end_cell [C] (device; t_end must then be
+// their maximum).
 int solve_device(cbx_network* net, const cbx_cell_params* phi, const double* x0, int C, double t0, double t_end,
-                 const cbx_options* opt, void* stream, double* x_out, int* cell_status, int max_grid);
+                 const cbx_options* opt, void* stream, double* x_out, int* cell_status, int max_grid,
+                 const double* t_end_cell = nullptr);
 // Set the calling thread's cbx_last_error() message; returns code.
 int record_error(int code, const std::string& msg);
 size_t device_smem_optin();

@@ -2,18 +2,29 @@
 //
 // Requests (a network, C cells, a time span, options) are submitted from any
 // host thread and admitted by a scheduler thread as soon as a CUDA stream of
-// the pool and enough of the device-memory budget are free; requests that
-// arrive while others run are admitted into the freed stream/memory and their
-// kernels run concurrently with the running ones. Each admitted request gets
-// its own device buffers (inputs, outputs, solver workspace), an H2D copy, a
-// solver launch with at most `max_ctas` persistent CTAs (so several requests,
-// of any network size, share the SMs; each CTA keeps a cell's solver state on
-// chip, retires it and back-fills from the request's cell counter), a D2H
-// copy and a stream-ordered free. A host callback marks it done. A cell's
-// result does not depend on the other requests in flight (fixed per-cell
-// arithmetic order), so results are the same alone and in the mix.
+// the pool and enough of the device-memory budget are free. Queued requests
+// for the same network with the same options and start time are merged into
+// one launch: their cells are concatenated (each keeps its own end time), so
+// the launch's persistent CTAs back-fill across requests; a cell's solver
+// state stays on chip for its whole solve. Requests that arrive while others
+// run are admitted into the freed streams and memory, and their kernels run
+// concurrently with the running ones; each launch uses at most `max_ctas`
+// CTAs so that several launches, of any network size, share the SMs.
+//
+// Per launch: device buffers (inputs, outputs, per-cell end times, solver
+// workspace), the H2D copies of every merged request (strided copies into the
+// [S][C] layout), the solver, the D2H copies back into each request's pinned
+// buffers, a stream-ordered free, and a host callback that completes the
+// requests. A cell's result does not depend on what else is in flight or in
+// the same launch (fixed per-cell arithmetic order), so results are the same
+// alone, merged and in the mix.
+//
+// Admission order: arrival order; a request that does not fit the free memory
+// may be passed by later, smaller ones at most kMaxPasses times, after which
+// nothing else is admitted before it.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -36,6 +47,9 @@ double now_s() {
 
 enum ReqState { kQueued = 0, kRunning = 1, kDone = 2, kFailed = 3 };
 
+constexpr int kMaxPasses = 8;            // times a waiting request may be passed by later ones
+constexpr int kMaxMergedCells = 1 << 16;  // cells of one merged launch
+
 }  // namespace
 
 struct cbx_server;
@@ -49,12 +63,21 @@ struct ServerRequest {
   cbx_options opt{};
   cbx_cell_params* h_phi = nullptr;  // pinned staging
   double* h_x = nullptr;             // pinned: x0 in, x_out back
+  double* h_tend = nullptr;          // pinned: t_end per cell
   int* h_status = nullptr;           // pinned
-  size_t bytes = 0;                  // device-memory reservation
-  int stream = -1;
   int state = kQueued;
   int rc = CBX_OK;
+  int passed = 0;                    // times a later request was admitted before it
   double t_submit = 0, t_start = 0, t_done = 0;
+};
+
+// One launch: one or more merged requests on one stream.
+struct ServerLaunch {
+  cbx_server* srv = nullptr;
+  std::vector<ServerRequest*> reqs;
+  int C = 0;
+  size_t bytes = 0;
+  int stream = -1;
 };
 
 struct cbx_server {
@@ -69,66 +92,143 @@ struct cbx_server {
   std::map<uint64_t, ServerRequest*> reqs;
   uint64_t next_id = 1;
   bool stop = false;
+  int waiting = 0;  // threads inside cbx_server_wait
   std::thread sched;
   size_t peak_in_use = 0;
   int peak_running = 0;
+  long long launches = 0, merged_requests = 0;
 };
 
 namespace {
 
-// Device bytes a request needs: inputs, outputs, status, workspace.
-size_t request_bytes(cbx_network* net, int C, bool mixed) {
+// Device bytes of a launch of C cells: inputs, outputs, end times, status, workspace.
+size_t launch_bytes(cbx_network* net, int C, bool mixed) {
   const HostNet& h = net->host;
   const SolverPlan p = plan_solver(h.S, h.R, h.nseg, h.nnzJ, mixed, h.head_ints);
   const int grid = std::max(1, std::min(C, std::max(1, p.occupancy) * device_sm_count()));
-  return (size_t)C * (sizeof(cbx_cell_params) + 2 * h.S * sizeof(double) + sizeof(int)) +
-         (size_t)grid * p.ws_stride * sizeof(double) + 4096;
+  return (size_t)C * (sizeof(cbx_cell_params) + 2 * h.S * sizeof(double) + sizeof(double) + sizeof(int)) +
+         (size_t)grid * p.ws_stride * sizeof(double) + 8192;
+}
+
+bool same_kind(const ServerRequest* a, const ServerRequest* b) {
+  return a->net == b->net && a->t0 == b->t0 && memcmp(&a->opt, &b->opt, sizeof(cbx_options)) == 0;
+}
+
+void free_request(ServerRequest* r) {
+  cudaFreeHost(r->h_phi);
+  cudaFreeHost(r->h_x);
+  cudaFreeHost(r->h_tend);
+  cudaFreeHost(r->h_status);
+  delete r;
 }
 
 void CUDART_CB on_done(void* arg) {
-  ServerRequest* r = (ServerRequest*)arg;
-  cbx_server* s = r->srv;
-  std::lock_guard<std::mutex> lock(s->mu);
-  r->t_done = now_s();
-  if (r->state == kRunning) r->state = r->rc == CBX_OK ? kDone : kFailed;
-  s->busy[r->stream] = 0;
-  s->in_use -= r->bytes;
+  ServerLaunch* L = (ServerLaunch*)arg;
+  cbx_server* s = L->srv;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    const double t = now_s();
+    for (ServerRequest* r : L->reqs) {
+      r->t_done = t;
+      if (r->state == kRunning) r->state = r->rc == CBX_OK ? kDone : kFailed;
+    }
+    s->busy[L->stream] = 0;
+    s->in_use -= L->bytes;
+  }
   s->cv.notify_all();
+  delete L;
 }
 
-void launch(cbx_server* s, ServerRequest* r) {
-  cudaStream_t st = s->streams[r->stream];
-  const size_t b_phi = (size_t)r->C * sizeof(cbx_cell_params), b_x = (size_t)r->S * r->C * sizeof(double),
-               b_st = (size_t)r->C * sizeof(int);
+void launch(cbx_server* s, ServerLaunch* L) {
+  cudaStream_t st = s->streams[L->stream];
+  ServerRequest* r0 = L->reqs[0];
+  const int C = L->C, S = r0->S;
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t b_phi = (size_t)C * sizeof(cbx_cell_params), b_x = (size_t)S * C * sizeof(double),
+               b_t = (size_t)C * sizeof(double), b_st = (size_t)C * sizeof(int);
   char* d = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&d, al(b_phi) + 2 * al(b_x) + al(b_st), st);
+  cudaError_t e = cudaMallocAsync((void**)&d, al(b_phi) + 2 * al(b_x) + al(b_t) + al(b_st), st);
   int rc = CBX_OK;
   if (e == cudaSuccess) {
     cbx_cell_params* d_phi = (cbx_cell_params*)d;
     double* d_x0 = (double*)(d + al(b_phi));
     double* d_xo = (double*)(d + al(b_phi) + al(b_x));
-    int* d_st = (int*)(d + al(b_phi) + 2 * al(b_x));
-    e = cudaMemcpyAsync(d_phi, r->h_phi, b_phi, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_x0, r->h_x, b_x, cudaMemcpyHostToDevice, st);
+    double* d_t = (double*)(d + al(b_phi) + 2 * al(b_x));
+    int* d_st = (int*)(d + al(b_phi) + 2 * al(b_x) + al(b_t));
+    double t_max = r0->t0;
+    int o = 0;
+    for (ServerRequest* r : L->reqs) {
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_phi + o, r->h_phi, r->C * sizeof(cbx_cell_params), cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess)  // x0 rows of this request into columns o..o+C_r-1 of [S][C]
+        e = cudaMemcpy2DAsync(d_x0 + o, C * sizeof(double), r->h_x, r->C * sizeof(double), r->C * sizeof(double), S,
+                              cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_t + o, r->h_tend, r->C * sizeof(double), cudaMemcpyHostToDevice, st);
+      t_max = std::max(t_max, r->t_end);
+      o += r->C;
+    }
     if (e == cudaSuccess) {
-      rc = solve_device(r->net, d_phi, d_x0, r->C, r->t0, r->t_end, &r->opt, st, d_xo, d_st, s->max_ctas);
-      if (rc == CBX_OK) {
-        e = cudaMemcpyAsync(r->h_x, d_xo, b_x, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(r->h_status, d_st, b_st, cudaMemcpyDeviceToHost, st);
+      rc = solve_device(r0->net, d_phi, d_x0, C, r0->t0, t_max, &r0->opt, st, d_xo, d_st, s->max_ctas, d_t);
+      o = 0;
+      for (ServerRequest* r : L->reqs) {
+        if (rc == CBX_OK && e == cudaSuccess)
+          e = cudaMemcpy2DAsync(r->h_x, r->C * sizeof(double), d_xo + o, C * sizeof(double), r->C * sizeof(double), S,
+                                cudaMemcpyDeviceToHost, st);
+        if (rc == CBX_OK && e == cudaSuccess)
+          e = cudaMemcpyAsync(r->h_status, d_st + o, r->C * sizeof(int), cudaMemcpyDeviceToHost, st);
+        o += r->C;
       }
     }
     cudaFreeAsync(d, st);
   }
   if (e != cudaSuccess && rc == CBX_OK) rc = CBX_E_CUDA;
-  r->rc = rc;
-  e = cudaLaunchHostFunc(st, on_done, r);
+  for (ServerRequest* r : L->reqs) r->rc = rc;
+  e = cudaLaunchHostFunc(st, on_done, L);
   if (e != cudaSuccess) {
     // no callback will come: finish the bookkeeping here
     cudaStreamSynchronize(st);
-    r->rc = CBX_E_CUDA;
-    on_done(r);
+    for (ServerRequest* r : L->reqs) r->rc = CBX_E_CUDA;
+    on_done(L);
   }
+}
+
+// Pick the next launch from the queue (lock held): the first request that
+// fits, unless an earlier one has been passed too often, plus the queued
+// requests of the same kind that fit with it. Returns null when nothing fits.
+ServerLaunch* next_launch(cbx_server* s) {
+  auto fits = [&](size_t bytes) { return s->in_use + bytes <= s->budget || s->in_use == 0; };
+  ServerRequest* head = nullptr;
+  for (ServerRequest* r : s->queue) {
+    const bool mixed = r->opt.precision == CBX_MIXED;
+    if (fits(launch_bytes(r->net, r->C, mixed))) {
+      head = r;
+      break;
+    }
+    if (r->passed >= kMaxPasses) return nullptr;  // it goes next, when memory frees up
+  }
+  if (!head) return nullptr;
+  ServerLaunch* L = new ServerLaunch();
+  L->srv = s;
+  const bool mixed = head->opt.precision == CBX_MIXED;
+  for (ServerRequest* r : s->queue) {
+    if (r != head && !(same_kind(r, head) && L->C > 0)) continue;
+    if (r == head || (L->C + r->C <= kMaxMergedCells && fits(launch_bytes(head->net, L->C + r->C, mixed)))) {
+      L->reqs.push_back(r);
+      L->C += r->C;
+    }
+  }
+  // head first in the launch: requests merged before it in arrival order were skipped above
+  L->bytes = launch_bytes(head->net, L->C, mixed);
+  for (ServerRequest* r : s->queue) {
+    if (r == head) break;
+    if (std::find(L->reqs.begin(), L->reqs.end(), r) == L->reqs.end()) r->passed++;
+  }
+  std::deque<ServerRequest*> rest;
+  for (ServerRequest* r : s->queue)
+    if (std::find(L->reqs.begin(), L->reqs.end(), r) == L->reqs.end()) rest.push_back(r);
+  s->queue.swap(rest);
+  return L;
 }
 
 void scheduler(cbx_server* s) {
@@ -136,34 +236,34 @@ void scheduler(cbx_server* s) {
   std::unique_lock<std::mutex> lock(s->mu);
   for (;;) {
     if (s->stop) break;
-    bool launched = false;
-    for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
-      ServerRequest* r = *it;
-      int free_stream = -1;
-      for (size_t k = 0; k < s->busy.size(); ++k)
-        if (!s->busy[k]) {
-          free_stream = (int)k;
-          break;
-        }
-      if (free_stream < 0) break;
-      if (s->in_use + r->bytes > s->budget && s->in_use > 0) continue;  // later, smaller requests may fit
-      s->queue.erase(it);
-      s->busy[free_stream] = 1;
-      s->in_use += r->bytes;
-      s->peak_in_use = std::max(s->peak_in_use, s->in_use);
-      int running = 0;
-      for (char b : s->busy) running += b;
-      s->peak_running = std::max(s->peak_running, running);
-      r->stream = free_stream;
-      r->state = kRunning;
-      r->t_start = now_s();
-      lock.unlock();
-      launch(s, r);
-      lock.lock();
-      launched = true;
-      break;  // the queue may have changed
+    int free_stream = -1;
+    for (size_t k = 0; k < s->busy.size(); ++k)
+      if (!s->busy[k]) {
+        free_stream = (int)k;
+        break;
+      }
+    ServerLaunch* L = free_stream >= 0 && !s->queue.empty() ? next_launch(s) : nullptr;
+    if (!L) {
+      s->cv.wait(lock);
+      continue;
     }
-    if (!launched) s->cv.wait(lock);
+    L->stream = free_stream;
+    s->busy[free_stream] = 1;
+    s->in_use += L->bytes;
+    s->peak_in_use = std::max(s->peak_in_use, s->in_use);
+    int running = 0;
+    for (char b : s->busy) running += b;
+    s->peak_running = std::max(s->peak_running, running);
+    s->launches++;
+    s->merged_requests += (long long)L->reqs.size() - 1;
+    const double t = now_s();
+    for (ServerRequest* r : L->reqs) {
+      r->state = kRunning;
+      r->t_start = t;
+    }
+    lock.unlock();
+    launch(s, L);
+    lock.lock();
   }
 }
 
@@ -176,14 +276,18 @@ int cbx_server_create(size_t mem_budget, int n_streams, int max_ctas, cbx_server
   *out = nullptr;
   if (n_streams < 1 || n_streams > 64) return record_error(CBX_E_ARG, "n_streams must be in 1..64");
   if (max_ctas < 0) return record_error(CBX_E_ARG, "max_ctas must be >= 0");
+  size_t free_b = 0, total_b = 0;
+  cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
+  if (e != cudaSuccess) return record_error(CBX_E_CUDA, std::string("cudaMemGetInfo: ") + cudaGetErrorString(e));
+  const size_t derived = free_b / 10 * 8;  // 80 % of the memory free now
   cbx_server* s = new (std::nothrow) cbx_server();
   if (!s) return record_error(CBX_E_NOMEM, "host allocation failed");
   cudaGetDevice(&s->device);
-  s->budget = mem_budget;
+  s->budget = mem_budget == 0 ? derived : std::min(mem_budget, derived);
   s->max_ctas = max_ctas;
   for (int k = 0; k < n_streams; ++k) {
     cudaStream_t st;
-    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
       for (cudaStream_t x : s->streams) cudaStreamDestroy(x);
       delete s;
@@ -202,6 +306,7 @@ int cbx_server_submit(cbx_server* s, cbx_network* net, const cbx_cell_params* ph
   if (!s || !net || !request_id) return record_error(CBX_E_ARG, "NULL argument");
   if (C < 1 || !phi || !x0) return record_error(CBX_E_ARG, "need C >= 1 and host arrays");
   if (!(t_end >= t0)) return record_error(CBX_E_ARG, "need t0 <= t_end");
+  if (C > kMaxMergedCells) return record_error(CBX_E_TOO_LARGE, "request has more cells than one launch takes (65536)");
   ServerRequest* r = new (std::nothrow) ServerRequest();
   if (!r) return record_error(CBX_E_NOMEM, "host allocation failed");
   r->srv = s;
@@ -212,29 +317,33 @@ int cbx_server_submit(cbx_server* s, cbx_network* net, const cbx_cell_params* ph
   r->t_end = t_end;
   cbx_default_options(&r->opt);
   if (opt) r->opt = *opt;
-  r->bytes = request_bytes(net, C, r->opt.precision == CBX_MIXED);
-  if (r->bytes > s->budget) {
+  if (launch_bytes(net, C, r->opt.precision == CBX_MIXED) > s->budget) {
     delete r;
     return record_error(CBX_E_TOO_LARGE, "request larger than the server's memory budget");
   }
   cudaError_t e = cudaMallocHost((void**)&r->h_phi, (size_t)C * sizeof(cbx_cell_params));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&r->h_x, (size_t)r->S * C * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&r->h_tend, (size_t)C * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&r->h_status, (size_t)C * sizeof(int));
   if (e != cudaSuccess) {
-    cudaFreeHost(r->h_phi);
-    cudaFreeHost(r->h_x);
-    cudaFreeHost(r->h_status);
-    delete r;
+    free_request(r);
     return record_error(CBX_E_NOMEM, "pinned staging allocation failed");
   }
   memcpy(r->h_phi, phi, (size_t)C * sizeof(cbx_cell_params));
   memcpy(r->h_x, x0, (size_t)r->S * C * sizeof(double));
-  std::lock_guard<std::mutex> lock(s->mu);
-  r->id = s->next_id++;
-  r->t_submit = now_s();
-  s->reqs[r->id] = r;
-  s->queue.push_back(r);
-  *request_id = r->id;
+  for (int c = 0; c < C; ++c) r->h_tend[c] = t_end;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (s->stop) {
+      free_request(r);
+      return record_error(CBX_E_ARG, "the server is being destroyed");
+    }
+    r->id = s->next_id++;
+    r->t_submit = now_s();
+    s->reqs[r->id] = r;
+    s->queue.push_back(r);
+    *request_id = r->id;
+  }
   s->cv.notify_all();
   return CBX_OK;
 }
@@ -256,7 +365,9 @@ int cbx_server_wait(cbx_server* s, uint64_t request_id, double* x_out, int* cell
   auto it = s->reqs.find(request_id);
   if (it == s->reqs.end()) return record_error(CBX_E_ARG, "unknown request id");
   ServerRequest* r = it->second;
+  s->waiting++;
   s->cv.wait(lock, [&] { return r->state >= kDone; });
+  s->waiting--;
   const int rc = r->rc;
   if (rc == CBX_OK) {
     if (x_out) memcpy(x_out, r->h_x, (size_t)r->S * r->C * sizeof(double));
@@ -267,12 +378,10 @@ int cbx_server_wait(cbx_server* s, uint64_t request_id, double* x_out, int* cell
     times[1] = r->t_start;
     times[2] = r->t_done;
   }
-  s->reqs.erase(it);
+  s->reqs.erase(request_id);
   lock.unlock();
-  cudaFreeHost(r->h_phi);
-  cudaFreeHost(r->h_x);
-  cudaFreeHost(r->h_status);
-  delete r;
+  s->cv.notify_all();  // cbx_server_destroy may wait for the last waiter
+  free_request(r);
   return rc == CBX_OK ? CBX_OK : record_error(rc, "request failed");
 }
 
@@ -285,26 +394,37 @@ int cbx_server_stats(cbx_server* s, size_t* peak_bytes, int* peak_running, int* 
   return CBX_OK;
 }
 
+int cbx_server_info(cbx_server* s, size_t* budget, long long* launches, long long* merged_requests) {
+  if (!s) return record_error(CBX_E_ARG, "server is NULL");
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (budget) *budget = s->budget;
+  if (launches) *launches = s->launches;
+  if (merged_requests) *merged_requests = s->merged_requests;
+  return CBX_OK;
+}
+
 int cbx_server_destroy(cbx_server* s) {
   if (!s) return CBX_OK;
   {
     std::unique_lock<std::mutex> lock(s->mu);
+    s->stop = true;
+    // queued requests will not run: fail them so that their waiters return
+    for (ServerRequest* r : s->queue) {
+      r->state = kFailed;
+      r->rc = CBX_E_ARG;
+      r->t_done = now_s();
+    }
+    s->queue.clear();
+    s->cv.notify_all();
     s->cv.wait(lock, [&] {
       for (char b : s->busy)
         if (b) return false;
-      return true;
+      return s->waiting == 0;
     });
-    s->stop = true;
-    s->cv.notify_all();
   }
   s->sched.join();
   for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
-  for (auto& kv : s->reqs) {
-    cudaFreeHost(kv.second->h_phi);
-    cudaFreeHost(kv.second->h_x);
-    cudaFreeHost(kv.second->h_status);
-    delete kv.second;
-  }
+  for (auto& kv : s->reqs) free_request(kv.second);
   delete s;
   return CBX_OK;
 }

@@ -1169,6 +1169,12 @@ __device__ cbx_cell_params track_params(const double* track, int K, int cell, do
                          fma(w, B[4] - A[4], A[4]), fma(w, B[5] - A[5], A[5])};
 }
 
+// The cell's end time: its own (merged requests of different spans in one
+// launch) or the launch's.
+__device__ __forceinline__ double cell_t_end(const SolveArgs& a, int cell) {
+  return a.t_end_cell ? a.t_end_cell[cell] : a.t_end;
+}
+
 // Every knot finite with n_H, T > 0, and the knot times strictly increasing.
 __device__ bool track_valid(const double* track, int K, int cell) {
   const double* k0 = track + (size_t)cell * K * 6;
@@ -1201,7 +1207,8 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
   rec.on = a.tape.nops != nullptr;
   for (int i = threadIdx.x; i < S; i += NT) s.y[i] = a.x0[(size_t)__ldg(n.perm + i) * a.C + cell];
   if (!(p.n_H > 0.0) || !(p.T > 0.0) || !isfinite(p.n_H) || !isfinite(p.T) || !isfinite(p.A_V) ||
-      !isfinite(p.G0) || !isfinite(p.zeta) || (a.track && !track_valid(a.track, a.K, cell))) {
+      !isfinite(p.G0) || !isfinite(p.zeta) || (a.track && !track_valid(a.track, a.K, cell)) ||
+      !(cell_t_end(a, cell) >= a.t0) || !isfinite(cell_t_end(a, cell))) {
     status = CBX_CELL_BAD_INPUT;
     __syncthreads();
     for (int i = threadIdx.x; i < S; i += NT) a.x_out[(size_t)__ldg(n.perm + i) * a.C + cell] = s.y[i];
@@ -1217,7 +1224,7 @@ __device__ void solve_cell(const SolveArgs& a, int cell, Smem& s, double* ws) {
         t_rates = tt;
       }
     };
-    const double rtol = a.rtol, atol = a.atol, t_end = a.t_end;
+    const double rtol = a.rtol, atol = a.atol, t_end = cell_t_end(a, cell);
     double* D = s.D;
     // f0 and the initial step (Hairer, Norsett & Wanner I, II.4, p = 1)
     rhs(n, c.kap, s.y, s.f, s.r, s.part);
@@ -1404,7 +1411,8 @@ __device__ void solve_cell_rk(const SolveArgs& a, int cell, Smem& s, double* ws)
   double* yprev = s.D + 6 * S;
   for (int i = threadIdx.x; i < S; i += NT) yn[i] = a.x0[(size_t)__ldg(n.perm + i) * a.C + cell];
   if (!(p.n_H > 0.0) || !(p.T > 0.0) || !isfinite(p.n_H) || !isfinite(p.T) || !isfinite(p.A_V) ||
-      !isfinite(p.G0) || !isfinite(p.zeta) || (a.track && !track_valid(a.track, a.K, cell))) {
+      !isfinite(p.G0) || !isfinite(p.zeta) || (a.track && !track_valid(a.track, a.K, cell)) ||
+      !(cell_t_end(a, cell) >= a.t0) || !isfinite(cell_t_end(a, cell))) {
     status = CBX_CELL_BAD_INPUT;
     __syncthreads();
     for (int i = threadIdx.x; i < S; i += NT) a.x_out[(size_t)__ldg(n.perm + i) * a.C + cell] = yn[i];
@@ -1419,7 +1427,7 @@ __device__ void solve_cell_rk(const SolveArgs& a, int cell, Smem& s, double* ws)
         t_rates = tt;
       }
     };
-    const double rtol = a.rtol, atol = a.atol, t_end = a.t_end;
+    const double rtol = a.rtol, atol = a.atol, t_end = cell_t_end(a, cell);
     const double gamma = a.rk_a[1][1];
     double* slot = s.red + 40;
     // f_1 and the initial step (Hairer, Norsett & Wanner I, II.4, p = 3)
