@@ -453,7 +453,9 @@ def run_gpu(args):
         blocks = (("adjoint", lambda: adjoint_block(carbox, dev, stream, n_checks=1)),
                   ("serving", lambda: serving_block(carbox, rate=200.0, duration=0.25)),
                   ("track", lambda: track_block(carbox, dev, stream, n_checks=1)),
-                  ("zeta", lambda: zeta_block(carbox, dev, stream, n_checks=1)))
+                  ("zeta", lambda: zeta_block(carbox, dev, stream, n_checks=1)),
+                  ("esdirk", lambda: esdirk_block(carbox, dev, stream)),
+                  ("hmc", lambda: hmc_block(carbox, dev, stream)))
         extras = {}
         with ClockSampler(local) as clk_x:
             for name, run in blocks:
@@ -807,6 +809,91 @@ def track_block(carbox, dev, stream, n_checks=1):
     return res
 
 
+def esdirk_block(carbox, dev, stream, n_err=3):
+    """ESDIRK 4(3) of Kvaerno's family (the paper's kind of solver) next to the BDF on the
+    same 4,096 cells of the 150-species network, 1 Myr, FP64 and mixed; and both methods'
+    error against an rtol-1e-8 oracle reference on n_err cells (cross-method parity)."""
+    import torch
+    net = synth.make_network(S_SP, R_RX)
+    N = carbox.Network.from_synth(net)
+    C = 4096
+    phi_h = synth.cells(C)
+    x0_h = np.repeat(synth.initial_abundances(net)[:, None], C, axis=1)
+    phi = torch.tensor(phi_h, device=dev).contiguous()
+    x0 = torch.tensor(x0_h, device=dev).contiguous()
+    res = {"config": "esdirk", "workload": f"{S_SP} species / {R_RX} reactions, {C} cells, 0 -> 1 Myr, rtol 1e-4, "
+                                           "atol 1e-20; ESDIRK 4(3) (5 stages, L-stable) vs BDF, same cells"}
+    xs = {}
+    for method, mname in ((carbox.CBX_METHOD_ESDIRK, "esdirk"), (carbox.CBX_METHOD_BDF, "bdf")):
+        for prec, pname in ((carbox.CBX_FP64, "fp64"), (carbox.CBX_MIXED, "mixed")):
+            o = carbox.options(rtol=RTOL, atol=ATOL, precision=prec, method=method)
+            carbox.solve(N, phi[:152].contiguous(), x0[:, :152].contiguous(), 0.0, T_END, o, stream=stream)
+            st = carbox.stats_tensor(C, dev)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            x, status, _ = carbox.solve(N, phi, x0, 0.0, T_END, o, stream=stream, stats=st)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            sd = carbox.stats_dict(st.cpu().numpy())
+            res[f"{mname}_{pname}"] = {"ms": ms, "value": C / (ms / 1e3), "unit": "cell-solves/s",
+                                       "cells_ok": int((status == 0).sum().item()),
+                                       "steps_per_cell": float(sd["steps"].mean()),
+                                       "lu_per_cell": float(sd["lu_factors"].mean()),
+                                       "rhs_per_cell": float(sd["rhs_evals"].mean())}
+            if pname == "fp64":
+                xs[mname] = x[:, :n_err].cpu().numpy()
+    tight = oracle_map(net, phi_h[:n_err], x0_h[:, 0], T_END, 1e-8, 1e-26)
+    errs = {}
+    for m in ("esdirk", "bdf"):
+        e = []
+        for c in range(n_err):
+            big = tight[:, c] > 1e-12
+            e.append(float(np.max(np.abs(xs[m][big, c] / tight[big, c] - 1))))
+        errs[m] = e
+    res["error_vs_rtol1e-8_oracle"] = {"cells": n_err, **errs}
+    return res
+
+
+def hmc_block(carbox, dev, stream, transitions=4, leapfrog=4):
+    """Rate-uncertainty sampling (HMC over ln alpha, the posterior gradient from one recorded
+    solve and the discrete adjoint): 150 species, 64 cells, 1e5 yr, 5 target species per
+    cell; time per transition and per posterior-gradient evaluation."""
+    import torch
+    from paper_2511_10558_gb300 import hmc
+    net = synth.make_network(S_SP, R_RX)
+    N = carbox.Network.from_synth(net)
+    C = 64
+    t_end = 1e5 * synth.YEAR
+    phi = torch.tensor(synth.cells(C, seed=31), device=dev).contiguous()
+    x0 = torch.tensor(np.repeat(synth.initial_abundances(net)[:, None], C, axis=1), device=dev).contiguous()
+    theta0 = np.log(net.alpha)
+    rng = np.random.default_rng(5)
+    theta_true = theta0 + 0.2 * rng.standard_normal(net.n_reactions)
+    xt, _ = carbox.solve_with_alpha(N, torch.tensor(np.exp(theta_true), device=dev), phi, x0, 0.0, t_end)
+    xt = xt.cpu().numpy()
+    targets = np.array([np.sort(rng.choice(np.flatnonzero(xt[:, c] > 1e-10), 5, replace=False)) for c in range(C)])
+    y = np.log10(xt[targets, np.arange(C)[:, None]])
+    post = hmc.RatePosterior(N, phi, x0, t_end, targets, y, 0.1, 0.5, theta0)
+    U, g = post(theta0)
+    t0 = time.perf_counter()
+    U, g = post(theta0)
+    t_eval = time.perf_counter() - t0
+    th, acc_n = theta0.copy(), 0
+    rng2 = np.random.default_rng(9)
+    t0 = time.perf_counter()
+    for _ in range(transitions):
+        th, U, g, acc, dH = hmc.hmc_step(th, U, g, post, 1e-3, leapfrog, rng2)
+        acc_n += int(acc)
+    dt = time.perf_counter() - t0
+    return {"config": "hmc", "workload": f"{S_SP} species / {R_RX} reactions, {C} cells, 0 -> 1e5 yr, FP64; "
+                                         f"theta = ln alpha [{net.n_reactions}], 5 targets per cell, sigma 0.1 dex, "
+                                         f"prior sd 0.5; {transitions} transitions of {leapfrog} leapfrog steps",
+            "s_per_posterior_gradient": t_eval, "s_per_transition": dt / transitions,
+            "accepted": acc_n, "transitions": transitions, "final_U": float(U)}
+
+
 def run_serving(args):
     """Config 5 alone, at the given rate and duration of arrivals."""
     torch, dev, carbox = _gpu_setup()
@@ -885,8 +972,8 @@ def main():
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the compact config 4/5, track and zeta runs")
     ap.add_argument("--no-peaks", action="store_true", help="skip the FMA peak probe (nominal peaks)")
-    ap.add_argument("--config", choices=["bench", "large", "adjoint", "serving", "zeta", "track", "peaks"],
-                    default="bench")
+    ap.add_argument("--config", choices=["bench", "large", "adjoint", "serving", "zeta", "track", "peaks", "esdirk",
+                                         "hmc"], default="bench")
     ap.add_argument("--duration", type=float, default=2.0, help="serving: seconds of Poisson arrivals")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean requests per second")
     args = ap.parse_args()
@@ -902,6 +989,10 @@ def main():
         run_zeta(args)
     elif args.config == "track":
         run_track(args)
+    elif args.config in ("esdirk", "hmc"):
+        torch, dev, carbox = _gpu_setup()
+        blk = esdirk_block if args.config == "esdirk" else hmc_block
+        print(json.dumps(blk(carbox, dev, torch.cuda.current_stream(dev))), flush=True)
     elif args.config == "peaks":
         torch, dev, carbox = _gpu_setup()
         with ClockSampler(0) as clk:

@@ -213,7 +213,9 @@ ServerLaunch* next_launch(cbx_server* s) {
   const bool mixed = head->opt.precision == CBX_MIXED;
   for (ServerRequest* r : s->queue) {
     if (r != head && !(same_kind(r, head) && L->C > 0)) continue;
-    if (r == head || (L->C + r->C <= kMaxMergedCells && fits(launch_bytes(head->net, L->C + r->C, mixed)))) {
+    // a merged launch must fit the budget itself (the head alone always may run on an idle server)
+    if (r == head ||
+        (L->C + r->C <= kMaxMergedCells && s->in_use + launch_bytes(head->net, L->C + r->C, mixed) <= s->budget)) {
       L->reqs.push_back(r);
       L->C += r->C;
     }

@@ -504,6 +504,10 @@ __device__ void backward_crout64(const double* M, int S, double* v) {
 
 constexpr int NB = 32;  // panel width
 
+#ifndef CBX_TC_LU
+#define CBX_TC_LU 1  // FP32 trailing updates of large networks on the tensor cores (mma.sync TF32, split form)
+#endif
+
 // Right-looking blocked LU without pivoting, panel width NB, on a dense
 // row-major matrix (leading dimension ld). Per panel: (1) the panel columns are
 // factored with one barrier per column, each thread keeping one row of the
@@ -683,10 +687,107 @@ __device__ __forceinline__ void trailing_update_ng(LT* M, int S, int ld, int kb,
   }
 }
 
+// ---- tensor-core form of the FP32 trailing update (mixed path)
+//
+// A22 -= L21 U12 is a dense contraction with K = nb <= 32: it runs on the
+// tensor cores as warp-level mma.sync m16n8k8 with TF32 operands, in the
+// split form a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (x_hi = tf32(x),
+// x_lo = tf32(x - x_hi)), which keeps the products at FP32 accuracy (the
+// dropped a_lo b_lo is ~2^-22 relative), so the factor is as good as the
+// FP32 FMA form and the FP64 refinement needs no more sweeps. Each warp
+// takes blocks of 16 rows x 8 TN columns; the A22 tile is the accumulator's
+// start value and -L21 the A operand, so D = A22 - L21 U12 directly.
+// Fragment layouts of m16n8k8 (g = lane / 4, q = lane % 4):
+//   A (16 x 8): a0 (g, q), a1 (g + 8, q), a2 (g, q + 4), a3 (g + 8, q + 4)
+//   B (8 x 8):  b0 (q, g), b1 (q + 4, g)
+//   C (16 x 8): c0 (g, 2q), c1 (g, 2q + 1), c2 (g + 8, 2q), c3 (g + 8, 2q + 1)
+
+__device__ __forceinline__ unsigned to_tf32(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void split_tf32(float x, unsigned& hi, unsigned& lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int TN>
+__device__ __forceinline__ void trailing_update_tc(float* M, int S, int ld, int kb, int nb) {
+  const int ke = kb + nb, m = S - ke;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  const int nbr = (m + 15) / 16, nbc = (m + 8 * TN - 1) / (8 * TN);
+  for (int blk = warp; blk < nbr * nbc; blk += NW) {
+    const int r0 = ke + (blk / nbc) * 16, c0 = ke + (blk % nbc) * 8 * TN;
+    const int ra = r0 + g, rb = r0 + g + 8;
+    // -L21 rows ra, rb (columns kb .. kb + nb - 1), split into hi and lo
+    unsigned ah[4][4], al[4][4];
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      const int k0 = 8 * ks + q, k1 = k0 + 4;
+      const float v0 = ra < S && k0 < nb ? -M[ra * ld + kb + k0] : 0.0f;
+      const float v1 = rb < S && k0 < nb ? -M[rb * ld + kb + k0] : 0.0f;
+      const float v2 = ra < S && k1 < nb ? -M[ra * ld + kb + k1] : 0.0f;
+      const float v3 = rb < S && k1 < nb ? -M[rb * ld + kb + k1] : 0.0f;
+      split_tf32(v0, ah[ks][0], al[ks][0]);
+      split_tf32(v1, ah[ks][1], al[ks][1]);
+      split_tf32(v2, ah[ks][2], al[ks][2]);
+      split_tf32(v3, ah[ks][3], al[ks][3]);
+    }
+#pragma unroll
+    for (int t = 0; t < TN; ++t) {
+      const int cb = c0 + 8 * t;        // first column of this n-tile
+      const int cc = cb + 2 * q;        // accumulator columns cc, cc + 1
+      const int cg = cb + g;            // B operand column
+      float d[4];
+      d[0] = ra < S && cc < S ? M[ra * ld + cc] : 0.0f;
+      d[1] = ra < S && cc + 1 < S ? M[ra * ld + cc + 1] : 0.0f;
+      d[2] = rb < S && cc < S ? M[rb * ld + cc] : 0.0f;
+      d[3] = rb < S && cc + 1 < S ? M[rb * ld + cc + 1] : 0.0f;
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {
+        if (8 * ks >= nb) break;
+        const int k0 = 8 * ks + q, k1 = k0 + 4;
+        const float u0 = cg < S && k0 < nb ? M[(kb + k0) * ld + cg] : 0.0f;
+        const float u1 = cg < S && k1 < nb ? M[(kb + k1) * ld + cg] : 0.0f;
+        unsigned bh0, bl0, bh1, bl1;
+        split_tf32(u0, bh0, bl0);
+        split_tf32(u1, bh1, bl1);
+        mma_tf32(d, al[ks], bh0, bh1);
+        mma_tf32(d, ah[ks], bl0, bl1);
+        mma_tf32(d, ah[ks], bh0, bh1);
+      }
+      if (ra < S && cc < S) M[ra * ld + cc] = d[0];
+      if (ra < S && cc + 1 < S) M[ra * ld + cc + 1] = d[1];
+      if (rb < S && cc < S) M[rb * ld + cc] = d[2];
+      if (rb < S && cc + 1 < S) M[rb * ld + cc + 1] = d[3];
+    }
+  }
+}
+
 template <typename LT, bool LARGE>
 __device__ __forceinline__ void trailing_update(LT* M, int S, int ld, int kb, int nb) {
   const int ncol = S - kb - nb;
   if (ncol <= 0) return;
+#if CBX_TC_LU
+  // tensor cores where they pay: the global-memory matrices of large networks
+  // (at 150 species, trailing blocks of <= 118 rows in shared memory, the FMA
+  // form below measured 2.5 % faster over a whole solve)
+  if constexpr (sizeof(LT) == 4 && LARGE) {
+    trailing_update_tc<4>((float*)M, S, ld, kb, nb);
+    __syncthreads();
+    return;
+  }
+#endif
   if (!LARGE) {
     switch ((ncol + 31) >> 5) {
       case 1: trailing_update_ng<LT, 1, 4>(M, S, ld, kb, nb); break;
