@@ -208,8 +208,7 @@ int cbx_esdirk_tableau(double* a, double* c, double* gamma);
 /*
  * Integrate C cells from t0 to t_end (seconds) with the variable-order BDF
  * (or the ESDIRK of cbx_esdirk_tableau when opt->method is CBX_METHOD_ESDIRK;
- * that method supports networks whose Newton matrix fits in shared memory,
- * S <= 256, and has no adjoint: recording entry points reject it).
+ * that method has no adjoint: recording entry points reject it).
  *   phi    [C]     device pointer, cell parameters (Sec. 2: k(phi)).
  *   x0     [S][C]  device pointer, initial abundances per n_H.
  *   opt            host pointer (NULL = defaults).

@@ -17,8 +17,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "lib", "libcarbox.so")
 SOURCES = ["solve_fp64.cu", "solve_fp64_gm.cu", "solve_mixed.cu", "solve_mixed_gm.cu", "solve_fp64_rk.cu",
-           "solve_mixed_rk.cu", "adjoint.cu", "plan.cu", "network.cpp", "capi.cpp", "esdirk.cpp", "noalloc.cu",
-           "server.cpp", "peaks.cu"]
+           "solve_mixed_rk.cu", "solve_fp64_gm_rk.cu", "solve_mixed_gm_rk.cu", "adjoint.cu", "plan.cu", "network.cpp",
+           "capi.cpp", "esdirk.cpp", "noalloc.cu", "server.cpp", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

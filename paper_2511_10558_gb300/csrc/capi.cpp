@@ -251,8 +251,6 @@ static int solve_impl(cbx_network* net, const cbx_cell_params* phi, const double
              h.S, h.R, plan.smem, 512, device_smem_optin());
     return fail(CBX_E_TOO_LARGE, m);
   }
-  if (rk && plan.gm)
-    return fail(CBX_E_TOO_LARGE, "CBX_METHOD_ESDIRK supports networks whose Newton matrix fits in shared memory");
   int grid = std::min(C, occ * device_sm_count());
   if (max_grid > 0) grid = std::min(grid, max_grid);
   cudaStream_t st = (cudaStream_t)stream;

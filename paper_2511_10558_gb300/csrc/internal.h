@@ -184,7 +184,9 @@ int occupancy_solve_mixed(size_t smem);
 int occupancy_solve_mixed_gm(size_t smem);
 int launch_solve_fp64_rk(const SolveArgs& a, size_t smem, int grid, void* stream);
 int launch_solve_mixed_rk(const SolveArgs& a, size_t smem, int grid, void* stream);
-// Launch the ESDIRK solver (shared-memory matrix only); returns a cudaError_t value.
+int launch_solve_fp64_gm_rk(const SolveArgs& a, size_t smem, int grid, void* stream);
+int launch_solve_mixed_gm_rk(const SolveArgs& a, size_t smem, int grid, void* stream);
+// Launch the ESDIRK solver; returns a cudaError_t value.
 int launch_solver_rk(const SolveArgs& a, const SolverPlan& p, int grid, void* stream);
 int device_sm_count();
 // cbx_solve on device buffers with at most max_grid CTAs (0: no cap) and,

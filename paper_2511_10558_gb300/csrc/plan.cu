@@ -63,7 +63,8 @@ size_t device_smem_optin() {
 int launch_solver_rk(const SolveArgs& a0, const SolverPlan& p, int grid, void* stream) {
   SolveArgs a = a0;
   a.piv_ints = p.piv_ints;
-  if (p.gm) return cudaErrorInvalidValue;
+  if (p.gm)
+    return p.mixed ? launch_solve_mixed_gm_rk(a, p.smem, grid, stream) : launch_solve_fp64_gm_rk(a, p.smem, grid, stream);
   return p.mixed ? launch_solve_mixed_rk(a, p.smem, grid, stream) : launch_solve_fp64_rk(a, p.smem, grid, stream);
 }
 

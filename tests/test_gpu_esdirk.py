@@ -8,8 +8,9 @@
 * Cross-method parity: at rtol 1e-4 the ESDIRK and BDF results both lie within
   the methods' global error (1e-2 relative) of an rtol-1e-8 oracle reference.
 * Tracks: a phi(t) track solved by the ESDIRK agrees with the oracle's ESDIRK.
-* Argument errors: no recording with the ESDIRK (no adjoint), no global-memory
-  networks (S > 256), unknown methods rejected.
+* 500 species (matrix in global memory): twin parity and conservation.
+* Argument errors: no recording with the ESDIRK (no adjoint), unknown methods
+  rejected.
 """
 import numpy as np
 import pytest
@@ -139,9 +140,21 @@ def test_esdirk_argument_errors(dev, net32):
         carbox.solve_record(N, tape, phi, x0, 0.0, 1e10, carbox.options(method=RK))
     with pytest.raises(carbox.CarboxError):
         carbox.solve(N, phi, x0, 0.0, 1e10, carbox.options(method=7))
-    net500 = synth.make_network(500, 6000)
-    N5 = carbox.Network.from_synth(net500)
-    x05 = torch.tensor(synth.initial_abundances(net500)[:, None], device=dev).contiguous()
-    with pytest.raises(carbox.CarboxError) as e:
-        carbox.solve(N5, phi, x05, 0.0, 1e10, carbox.options(method=RK))
-    assert e.value.code == carbox.CBX_E_TOO_LARGE
+
+
+@pytest.mark.parametrize("prec", [carbox.CBX_FP64, carbox.CBX_MIXED])
+def test_large_500_twin(dev, prec):
+    # 500 species: the Newton matrix in each CTA's global workspace
+    net = synth.make_network(500, 6000)
+    N = carbox.Network.from_synth(net)
+    C = 3
+    phi = synth.cells(C, seed=37)
+    x0 = np.repeat(synth.initial_abundances(net)[:, None], C, axis=1)
+    t_end = 1e5 * YR
+    x, st, _ = _solve(N, phi, x0, t_end, dev, precision=prec, method=RK)
+    assert np.all(st == carbox.CBX_CELL_OK)
+    ref = parity.oracle_cells(net, phi[:2], x0[:, :2], t_end, method="esdirk")
+    for c in range(C):
+        assert _conserved(net, x0[:, c], x[:, c]), c
+    for c in range(2):
+        assert parity.max_rel(x[:, c], ref[:, c]) <= 1e-4, c
