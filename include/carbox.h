@@ -256,8 +256,10 @@ int cbx_solve_host(cbx_network* net, const cbx_cell_params* phi, const double* x
 
 /*
  * Replace the alpha parameters of all reactions (host pointer, R values) in the
- * network, on the host and on its device. Synchronous. Used to differentiate
- * with respect to ln alpha (Sec. 3: sensitivity to rate coefficients).
+ * network, on the host and on its device, for every later solve. Synchronous.
+ * Every user of the network sees the change; to solve with other alpha values
+ * for one call only (differentiation in ln alpha, Sec. 3), use
+ * cbx_solve_with_alpha, which leaves the network unchanged.
  */
 int cbx_network_set_alpha(cbx_network* net, const double* alpha);
 
