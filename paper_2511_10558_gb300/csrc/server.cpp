@@ -22,6 +22,10 @@
 // Admission order: arrival order; a request that does not fit the free memory
 // may be passed by later, smaller ones at most kMaxPasses times, after which
 // nothing else is admitted before it.
+//
+// Locking: no CUDA call is made while the server's mutex is held, because the
+// completion callback runs on a CUDA driver thread and takes that mutex; a
+// request's launch sizing is therefore computed at submit, outside the lock.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -68,6 +72,10 @@ struct ServerRequest {
   int state = kQueued;
   int rc = CBX_OK;
   int passed = 0;                    // times a later request was admitted before it
+  // launch sizing, computed at submit (no CUDA call may run under the server's
+  // lock: the completion callback, on a driver thread, takes that lock)
+  size_t cell_bytes = 0, cta_bytes = 0;
+  int grid_cap = 1;
   double t_submit = 0, t_start = 0, t_done = 0;
 };
 
@@ -101,13 +109,21 @@ struct cbx_server {
 
 namespace {
 
-// Device bytes of a launch of C cells: inputs, outputs, end times, status, workspace.
-size_t launch_bytes(cbx_network* net, int C, bool mixed) {
-  const HostNet& h = net->host;
-  const SolverPlan p = plan_solver(h.S, h.R, h.nseg, h.nnzJ, mixed, h.head_ints);
-  const int grid = std::max(1, std::min(C, std::max(1, p.occupancy) * device_sm_count()));
-  return (size_t)C * (sizeof(cbx_cell_params) + 2 * h.S * sizeof(double) + sizeof(double) + sizeof(int)) +
-         (size_t)grid * p.ws_stride * sizeof(double) + 8192;
+// Launch sizing of a request's kind (network, precision, CTA cap): CUDA calls,
+// so only outside the server's lock.
+void size_request(ServerRequest* r, int max_ctas) {
+  const HostNet& h = r->net->host;
+  const SolverPlan p = plan_solver(h.S, h.R, h.nseg, h.nnzJ, r->opt.precision == CBX_MIXED, h.head_ints);
+  r->cell_bytes = sizeof(cbx_cell_params) + 2 * h.S * sizeof(double) + sizeof(double) + sizeof(int);
+  r->cta_bytes = (size_t)p.ws_stride * sizeof(double);
+  r->grid_cap = std::max(1, std::max(1, p.occupancy) * device_sm_count());
+  if (max_ctas > 0) r->grid_cap = std::min(r->grid_cap, max_ctas);
+}
+
+// Device bytes of a launch of C cells of r's kind: inputs, outputs, end times,
+// status, workspace (pure arithmetic: safe under the lock).
+size_t launch_bytes(const ServerRequest* r, int C) {
+  return (size_t)C * r->cell_bytes + (size_t)std::min(C, r->grid_cap) * r->cta_bytes + 8192;
 }
 
 bool same_kind(const ServerRequest* a, const ServerRequest* b) {
@@ -200,8 +216,7 @@ ServerLaunch* next_launch(cbx_server* s) {
   auto fits = [&](size_t bytes) { return s->in_use + bytes <= s->budget || s->in_use == 0; };
   ServerRequest* head = nullptr;
   for (ServerRequest* r : s->queue) {
-    const bool mixed = r->opt.precision == CBX_MIXED;
-    if (fits(launch_bytes(r->net, r->C, mixed))) {
+    if (fits(launch_bytes(r, r->C))) {
       head = r;
       break;
     }
@@ -210,18 +225,16 @@ ServerLaunch* next_launch(cbx_server* s) {
   if (!head) return nullptr;
   ServerLaunch* L = new ServerLaunch();
   L->srv = s;
-  const bool mixed = head->opt.precision == CBX_MIXED;
   for (ServerRequest* r : s->queue) {
     if (r != head && !(same_kind(r, head) && L->C > 0)) continue;
     // a merged launch must fit the budget itself (the head alone always may run on an idle server)
-    if (r == head ||
-        (L->C + r->C <= kMaxMergedCells && s->in_use + launch_bytes(head->net, L->C + r->C, mixed) <= s->budget)) {
+    if (r == head || (L->C + r->C <= kMaxMergedCells && s->in_use + launch_bytes(head, L->C + r->C) <= s->budget)) {
       L->reqs.push_back(r);
       L->C += r->C;
     }
   }
   // head first in the launch: requests merged before it in arrival order were skipped above
-  L->bytes = launch_bytes(head->net, L->C, mixed);
+  L->bytes = launch_bytes(head, L->C);
   for (ServerRequest* r : s->queue) {
     if (r == head) break;
     if (std::find(L->reqs.begin(), L->reqs.end(), r) == L->reqs.end()) r->passed++;
@@ -319,7 +332,8 @@ int cbx_server_submit(cbx_server* s, cbx_network* net, const cbx_cell_params* ph
   r->t_end = t_end;
   cbx_default_options(&r->opt);
   if (opt) r->opt = *opt;
-  if (launch_bytes(net, C, r->opt.precision == CBX_MIXED) > s->budget) {
+  size_request(r, s->max_ctas);
+  if (launch_bytes(r, C) > s->budget) {
     delete r;
     return record_error(CBX_E_TOO_LARGE, "request larger than the server's memory budget");
   }
@@ -335,8 +349,9 @@ int cbx_server_submit(cbx_server* s, cbx_network* net, const cbx_cell_params* ph
   memcpy(r->h_x, x0, (size_t)r->S * C * sizeof(double));
   for (int c = 0; c < C; ++c) r->h_tend[c] = t_end;
   {
-    std::lock_guard<std::mutex> lock(s->mu);
+    std::unique_lock<std::mutex> lock(s->mu);
     if (s->stop) {
+      lock.unlock();
       free_request(r);
       return record_error(CBX_E_ARG, "the server is being destroyed");
     }
