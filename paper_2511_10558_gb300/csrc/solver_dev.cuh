@@ -504,10 +504,6 @@ __device__ void backward_crout64(const double* M, int S, double* v) {
 
 constexpr int NB = 32;  // panel width
 
-#ifndef CBX_WS_PANEL
-#define CBX_WS_PANEL 1  // FP32 panels: warp-synchronous diagonal block, two barriers per panel
-#endif
-
 #ifndef CBX_TC_LU
 #define CBX_TC_LU 1  // FP32 trailing updates of large networks on the tensor cores (mma.sync TF32, split form)
 #endif
@@ -577,54 +573,6 @@ __device__ __forceinline__ void panel_factor(LT* M, LT* invd, int S, int ld, int
       for (int jj = 0; jj < NB; ++jj)
         if (kb + jj < i) M[i * ld + kb + jj] = r[p][jj];
     }
-  }
-  __syncthreads();
-}
-
-// FP32 panel factorisation with two barriers instead of one per column.
-// Every pivot row of a full panel (rows kb .. kb + 31) belongs to warp 0, so
-// warp 0 factors the 32 x 32 diagonal block alone, in place in shared memory
-// (lane l owns row kb + l; a warp barrier after each column makes the pivot
-// row visible); after one CTA barrier the rows below eliminate their 32
-// columns in registers with the finished block, independently of each other.
-// Each element sees the same operations in the same order as in
-// panel_factor, so the factors are bitwise the same.
-template <int RPT>
-__device__ __forceinline__ void panel_factor_ws(float* M, float* invd, int S, int ld, int kb) {
-  const int tid = threadIdx.x, lane = tid & 31;
-  if (tid < 32) {
-    float* blk = M + kb * ld + kb;
-    float* row = blk + lane * ld;
-    for (int c = 0; c < NB; ++c) {
-      const float* prow = blk + c * ld;
-      const float inv = recip(prow[c]);
-      if (lane > c) {
-        const float l = row[c] * inv;
-        row[c] = l;
-        for (int jj = c + 1; jj < NB; ++jj) row[jj] -= l * prow[jj];
-      }
-      if (lane == 0) invd[kb + c] = inv;
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int p = 0; p < RPT; ++p) {
-    const int i = kb + tid + NT * p;
-    if (i < kb + NB || i >= S) continue;
-    float r[NB];
-#pragma unroll
-    for (int jj = 0; jj < NB; ++jj) r[jj] = M[i * ld + kb + jj];
-#pragma unroll
-    for (int c = 0; c < NB; ++c) {
-      const float* prow = M + (kb + c) * ld + kb;
-      const float l = r[c] * invd[kb + c];
-      r[c] = l;
-#pragma unroll
-      for (int jj = c + 1; jj < NB; ++jj) r[jj] -= l * prow[jj];
-    }
-#pragma unroll
-    for (int jj = 0; jj < NB; ++jj) M[i * ld + kb + jj] = r[jj];
   }
   __syncthreads();
 }
@@ -958,16 +906,8 @@ __device__ void lu_blocked(LT* M, LT* invd, int S, int ld) {
     const int nb = min(NB, S - kb);
     const bool two = LARGE && S - kb > NT;  // more panel rows than threads
     if (nb == NB) {
-#if CBX_WS_PANEL
-      if constexpr (sizeof(LT) == 4) {
-        if (two) panel_factor_ws<LARGE ? 2 : 1>((float*)M, (float*)invd, S, ld, kb);
-        else panel_factor_ws<1>((float*)M, (float*)invd, S, ld, kb);
-      } else
-#endif
-      {
-        if (two) panel_factor<LT, true, LARGE ? 2 : 1>(M, invd, S, ld, kb, nb);
-        else panel_factor<LT, true, 1>(M, invd, S, ld, kb, nb);
-      }
+      if (two) panel_factor<LT, true, LARGE ? 2 : 1>(M, invd, S, ld, kb, nb);
+      else panel_factor<LT, true, 1>(M, invd, S, ld, kb, nb);
       panel_u12<LT, true>(M, S, ld, kb, nb);
     } else {
       panel_factor<LT, false, 1>(M, invd, S, ld, kb, nb);
