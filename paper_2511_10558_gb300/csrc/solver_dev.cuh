@@ -381,12 +381,131 @@ __device__ __forceinline__ void crout_rows(const PivLists& P, double* M, double*
   }
 }
 
+// Dense range, R pivots per barrier (R = 1 or 2): U rows k .. k+R-1 are final
+// on entry; every later row i takes their updates, all columns j >= k+R. For
+// R = 2 the L entry of column k+1 is formed first, b = M[i][k+1] - M[i][k]
+// U[k][k+1], then each element takes -M[i][k] U[k][j] and -b U[k+1][j] in
+// that order: the operations, and so the roundings, of two single-pivot
+// steps. Warp 0 takes rows p = k+R and p+1 and finishes both as U rows
+// (reciprocal pivot, pivot p applied to row p+1 from registers, scaling), so
+// that the next step finds them final; the other warps take the rows from
+// p+2 on, two at a time.
+#ifndef CBX_DENSE_PAIRS
+#define CBX_DENSE_PAIRS 1
+#endif
+
+template <int MC, int R>
+__device__ __forceinline__ void dense_rank_rows(double* M, double* invd, int S, int k) {
+  const int ld = lead_dim(S);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c0 = k + R, nu = S - c0;  // columns c0 .. S-1, lane + 32 m
+  double u0[MC], u1[MC];
+#pragma unroll
+  for (int m = 0; m < MC; ++m) {
+    const bool in = lane + 32 * m < nu;
+    u0[m] = in ? M[k * ld + c0 + lane + 32 * m] : 0.0;
+    u1[m] = R == 2 && in ? M[(k + 1) * ld + c0 + lane + 32 * m] : 0.0;
+  }
+  const double u01 = R == 2 ? M[k * ld + k + 1] : 0.0;  // U(k, k+1)
+  // one row's update into x; returns its L entry of column k+1 (R = 2)
+  auto row_update = [&](const double* r, double (&x)[MC]) {
+    const double a = r[k];
+    const double b = R == 2 ? fma(-a, u01, r[k + 1]) : 0.0;
+#pragma unroll
+    for (int m = 0; m < MC; ++m) x[m] = lane + 32 * m < nu ? r[c0 + lane + 32 * m] : 0.0;
+#pragma unroll
+    for (int m = 0; m < MC; ++m) x[m] = fma(-a, u0[m], x[m]);
+    if (R == 2) {
+#pragma unroll
+      for (int m = 0; m < MC; ++m) x[m] = fma(-b, u1[m], x[m]);
+    }
+    return b;
+  };
+  if (w == 0) {
+    const int p = c0;
+    double* rp = M + p * ld;
+    double up[MC];  // row p: the diagonal at e = 0, U(p, :) after it
+    const double bp = row_update(rp, up);
+    const double inv_p = __drcp_rn(__shfl_sync(FULL, up[0], 0));  // column p: lane 0, group 0
+#pragma unroll
+    for (int m = 0; m < MC; ++m)
+      if (lane + 32 * m >= 1) up[m] *= inv_p;
+    if (lane == 0) {
+      invd[p] = inv_p;
+      if (R == 2) rp[k + 1] = bp;
+    }
+#pragma unroll
+    for (int m = 0; m < MC; ++m)
+      if (lane + 32 * m < nu) rp[c0 + lane + 32 * m] = up[m];
+    if (p + 1 < S) {
+      double* rq = rp + ld;
+      double xq[MC];
+      const double bq = row_update(rq, xq);
+      const double ap = __shfl_sync(FULL, xq[0], 0);  // L(p+1, p), stays
+#pragma unroll
+      for (int m = 0; m < MC; ++m)
+        if (lane + 32 * m >= 1) xq[m] = fma(-ap, up[m], xq[m]);
+      const double inv_q = __drcp_rn(__shfl_sync(FULL, xq[0], 1));  // column p+1: lane 1, group 0
+      if (lane == 0) {
+        invd[p + 1] = inv_q;
+        if (R == 2) rq[k + 1] = bq;
+      }
+#pragma unroll
+      for (int m = 0; m < MC; ++m) {
+        const int e = lane + 32 * m;
+        if (e < nu) rq[c0 + e] = e <= 1 ? xq[m] : xq[m] * inv_q;
+      }
+    }
+    return;
+  }
+  const int first = c0 + 2, nrow = S - first, nw = NW - 1;
+  for (int e = w - 1; e < nrow; e += 2 * nw) {
+    const bool two = e + nw < nrow;
+    double* r0 = M + (first + e) * ld;
+    double* r1 = two ? r0 + nw * ld : r0;
+    double x0[MC], x1[MC];
+    const double b0 = row_update(r0, x0);
+    double b1 = 0.0;
+    if (two) b1 = row_update(r1, x1);
+    if (R == 2 && lane == 0) {
+      r0[k + 1] = b0;
+      if (two) r1[k + 1] = b1;
+    }
+#pragma unroll
+    for (int m = 0; m < MC; ++m) {
+      if (lane + 32 * m < nu) {
+        r0[c0 + lane + 32 * m] = x0[m];
+        if (two) r1[c0 + lane + 32 * m] = x1[m];
+      }
+    }
+  }
+}
+
+// at most DENSE_PAIR_COLS columns (4 groups per lane): the step's register
+// footprint stays within the kernel's budget
+constexpr int DENSE_PAIR_COLS = 128;
+
+template <int R>
+__device__ __forceinline__ void dense_rank_step(double* M, double* invd, int S, int k) {
+  switch ((S - k - R + 31) >> 5) {
+    case 1: dense_rank_rows<1, R>(M, invd, S, k); break;
+    case 2: dense_rank_rows<2, R>(M, invd, S, k); break;
+    case 3: dense_rank_rows<3, R>(M, invd, S, k); break;
+    default: dense_rank_rows<4, R>(M, invd, S, k); break;
+  }
+}
+
 __device__ void lu_crout64(const PivLists& P, double* M, double* invd) {
   const int S = P.S, ld = lead_dim(S), kd = P.kd;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (w == 0) prep_pivot(P, M, invd, 0, lane);
   __syncthreads();
-  for (int k = 0; k + 1 < S; ++k) {
+  // with pairs, the single-pivot loop stops at kp: the first dense pivot
+  // with at most DENSE_PAIR_COLS columns after it
+  const int kp = max(kd, S - 1 - DENSE_PAIR_COLS);
+  const bool pairs = CBX_DENSE_PAIRS && S - kp >= 3;
+  const int k_single = pairs ? kp : S - 1;
+  for (int k = 0; k < k_single; ++k) {
     const bool dense = k >= kd;
     int l0, l1, u0, nu;
     if (dense) {
@@ -417,6 +536,16 @@ __device__ void lu_crout64(const PivLists& P, double* M, double* invd) {
       prep_pivot(P, M, invd, k + 1, lane);
     }
     __syncthreads();
+  }
+  if (pairs) {
+    // U row kp is final; pivot kp alone brings rows kp+1 and kp+2 to final,
+    // then pivots go in pairs while rows remain below them
+    dense_rank_step<1>(M, invd, S, kp);
+    __syncthreads();
+    for (int k = kp + 1; k + 2 < S; k += 2) {
+      dense_rank_step<2>(M, invd, S, k);
+      __syncthreads();
+    }
   }
   // L(:,k) /= pivot_k: M now holds L (unit lower), the pivots in invd (as
   // reciprocals) and U (unit upper), so both triangular solves are unit.
@@ -721,55 +850,64 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// A[r][c] -= sum_{k0 <= k < k0 + K} A[r][k] A[k][c] for r in [r0, r1), c in
+// [c0, c1) (the L columns and U rows of the K panels, in place), K taken in
+// chunks of 32 with the accumulator tiles kept in registers across chunks, so
+// that every element of the rectangle is read and written once.
 template <int TN>
-__device__ __forceinline__ void trailing_update_tc(float* M, int S, int ld, int kb, int nb) {
-  const int ke = kb + nb, m = S - ke;
+__device__ __forceinline__ void tc_rect(float* M, int ld, int k0, int K, int r0, int r1, int c0, int c1) {
+  const int m = r1 - r0, n = c1 - c0;
+  if (m <= 0 || n <= 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
-  const int nbr = (m + 15) / 16, nbc = (m + 8 * TN - 1) / (8 * TN);
+  const int nbr = (m + 15) / 16, nbc = (n + 8 * TN - 1) / (8 * TN);
   for (int blk = warp; blk < nbr * nbc; blk += NW) {
-    const int r0 = ke + (blk / nbc) * 16, c0 = ke + (blk % nbc) * 8 * TN;
-    const int ra = r0 + g, rb = r0 + g + 8;
-    // -L21 rows ra, rb (columns kb .. kb + nb - 1), split into hi and lo
-    unsigned ah[4][4], al[4][4];
+    const int rt = r0 + (blk / nbc) * 16, ct = c0 + (blk % nbc) * 8 * TN;
+    const int ra = rt + g, rb = rt + g + 8;
+    const bool oka = ra < r1, okb = rb < r1;
+    float d[TN][4];
 #pragma unroll
-    for (int ks = 0; ks < 4; ++ks) {
-      const int k0 = 8 * ks + q, k1 = k0 + 4;
-      const float v0 = ra < S && k0 < nb ? -M[ra * ld + kb + k0] : 0.0f;
-      const float v1 = rb < S && k0 < nb ? -M[rb * ld + kb + k0] : 0.0f;
-      const float v2 = ra < S && k1 < nb ? -M[ra * ld + kb + k1] : 0.0f;
-      const float v3 = rb < S && k1 < nb ? -M[rb * ld + kb + k1] : 0.0f;
-      split_tf32(v0, ah[ks][0], al[ks][0]);
-      split_tf32(v1, ah[ks][1], al[ks][1]);
-      split_tf32(v2, ah[ks][2], al[ks][2]);
-      split_tf32(v3, ah[ks][3], al[ks][3]);
+    for (int t = 0; t < TN; ++t) {
+      const int cc = ct + 8 * t + 2 * q;
+      d[t][0] = oka && cc < c1 ? M[ra * ld + cc] : 0.0f;
+      d[t][1] = oka && cc + 1 < c1 ? M[ra * ld + cc + 1] : 0.0f;
+      d[t][2] = okb && cc < c1 ? M[rb * ld + cc] : 0.0f;
+      d[t][3] = okb && cc + 1 < c1 ? M[rb * ld + cc + 1] : 0.0f;
+    }
+    for (int kc = 0; kc < K; kc += 32) {
+      const int kn = min(32, K - kc), kk = k0 + kc;
+      // -L rows ra, rb (columns kk .. kk + kn - 1), split into hi and lo
+      unsigned ah[4][4], al[4][4];
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {
+        const int e0 = 8 * ks + q, e1 = e0 + 4;
+        split_tf32(oka && e0 < kn ? -M[ra * ld + kk + e0] : 0.0f, ah[ks][0], al[ks][0]);
+        split_tf32(okb && e0 < kn ? -M[rb * ld + kk + e0] : 0.0f, ah[ks][1], al[ks][1]);
+        split_tf32(oka && e1 < kn ? -M[ra * ld + kk + e1] : 0.0f, ah[ks][2], al[ks][2]);
+        split_tf32(okb && e1 < kn ? -M[rb * ld + kk + e1] : 0.0f, ah[ks][3], al[ks][3]);
+      }
+#pragma unroll
+      for (int t = 0; t < TN; ++t) {
+        const int cg = ct + 8 * t + g;  // B operand column
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+          if (8 * ks >= kn) break;
+          const int e0 = 8 * ks + q, e1 = e0 + 4;
+          unsigned bh0, bl0, bh1, bl1;
+          split_tf32(cg < c1 && e0 < kn ? M[(kk + e0) * ld + cg] : 0.0f, bh0, bl0);
+          split_tf32(cg < c1 && e1 < kn ? M[(kk + e1) * ld + cg] : 0.0f, bh1, bl1);
+          mma_tf32(d[t], al[ks], bh0, bh1);
+          mma_tf32(d[t], ah[ks], bl0, bl1);
+          mma_tf32(d[t], ah[ks], bh0, bh1);
+        }
+      }
     }
 #pragma unroll
     for (int t = 0; t < TN; ++t) {
-      const int cb = c0 + 8 * t;        // first column of this n-tile
-      const int cc = cb + 2 * q;        // accumulator columns cc, cc + 1
-      const int cg = cb + g;            // B operand column
-      float d[4];
-      d[0] = ra < S && cc < S ? M[ra * ld + cc] : 0.0f;
-      d[1] = ra < S && cc + 1 < S ? M[ra * ld + cc + 1] : 0.0f;
-      d[2] = rb < S && cc < S ? M[rb * ld + cc] : 0.0f;
-      d[3] = rb < S && cc + 1 < S ? M[rb * ld + cc + 1] : 0.0f;
-#pragma unroll
-      for (int ks = 0; ks < 4; ++ks) {
-        if (8 * ks >= nb) break;
-        const int k0 = 8 * ks + q, k1 = k0 + 4;
-        const float u0 = cg < S && k0 < nb ? M[(kb + k0) * ld + cg] : 0.0f;
-        const float u1 = cg < S && k1 < nb ? M[(kb + k1) * ld + cg] : 0.0f;
-        unsigned bh0, bl0, bh1, bl1;
-        split_tf32(u0, bh0, bl0);
-        split_tf32(u1, bh1, bl1);
-        mma_tf32(d, al[ks], bh0, bh1);
-        mma_tf32(d, ah[ks], bl0, bl1);
-        mma_tf32(d, ah[ks], bh0, bh1);
-      }
-      if (ra < S && cc < S) M[ra * ld + cc] = d[0];
-      if (ra < S && cc + 1 < S) M[ra * ld + cc + 1] = d[1];
-      if (rb < S && cc < S) M[rb * ld + cc] = d[2];
-      if (rb < S && cc + 1 < S) M[rb * ld + cc + 1] = d[3];
+      const int cc = ct + 8 * t + 2 * q;
+      if (oka && cc < c1) M[ra * ld + cc] = d[t][0];
+      if (oka && cc + 1 < c1) M[ra * ld + cc + 1] = d[t][1];
+      if (okb && cc < c1) M[rb * ld + cc] = d[t][2];
+      if (okb && cc + 1 < c1) M[rb * ld + cc + 1] = d[t][3];
     }
   }
 }
@@ -783,7 +921,7 @@ __device__ __forceinline__ void trailing_update(LT* M, int S, int ld, int kb, in
   // (at 150 species, trailing blocks of <= 118 rows in shared memory, the FMA
   // form below measured 2.5 % faster over a whole solve)
   if constexpr (sizeof(LT) == 4 && LARGE) {
-    trailing_update_tc<4>((float*)M, S, ld, kb, nb);
+    tc_rect<4>((float*)M, ld, kb, nb, kb + nb, S, kb + nb, S);
     __syncthreads();
     return;
   }
@@ -898,10 +1036,63 @@ __device__ void invert_upper_blocks(LT* M, const LT* invd, int S, int ld) {
   __syncthreads();
 }
 
+// FP32, matrix in global memory: panels in pairs, so that the trailing matrix
+// is read and written once per two panels (its passes are the DRAM traffic of
+// the factorisation). For panels P1 = [kb, k2) and P2 = [k2, ke): factor P1
+// and form its U rows over all later columns; update only what P2 needs - its
+// columns (rows >= k2) and its U rows (columns >= ke) - from P1; factor P2 and
+// form its U rows; then one update of the rows and columns >= ke with K = 64
+// (both panels' L columns and U rows, contiguous in place). Not inlined: its
+// own register allocation keeps the kernel body free of spills (inlined, the
+// kernel spilled 1.7 KB).
+#ifndef CBX_PAIR_PANELS
+#define CBX_PAIR_PANELS 1
+#endif
+
+__device__ __forceinline__ void panel_factor_full_rows(float* M, float* invd, int S, int ld, int kb) {
+  if (S - kb > NT) panel_factor<float, true, 2>(M, invd, S, ld, kb, NB);
+  else panel_factor<float, true, 1>(M, invd, S, ld, kb, NB);
+}
+
+__device__ __noinline__ void lu_blocked_pairs(float* M, float* invd, int S, int ld) {
+  int kb = 0;
+  for (; kb + 2 * NB < S; kb += 2 * NB) {  // pairs with a trailing matrix after them
+    const int k2 = kb + NB, ke = kb + 2 * NB;
+    panel_factor_full_rows(M, invd, S, ld, kb);
+    panel_u12<float, true>(M, S, ld, kb, NB);
+    tc_rect<4>(M, ld, kb, NB, k2, S, k2, ke);   // P2's columns
+    tc_rect<4>(M, ld, kb, NB, k2, ke, ke, S);   // P2's U rows (disjoint from the above)
+    __syncthreads();
+    panel_factor_full_rows(M, invd, S, ld, k2);
+    panel_u12<float, true>(M, S, ld, k2, NB);
+    tc_rect<4>(M, ld, kb, 2 * NB, ke, S, ke, S);
+    __syncthreads();
+  }
+  for (; kb < S; kb += NB) {  // what is left: single panels
+    const int nb = min(NB, S - kb);
+    if (nb == NB) {
+      panel_factor_full_rows(M, invd, S, ld, kb);
+      panel_u12<float, true>(M, S, ld, kb, nb);
+    } else {
+      panel_factor<float, false, 1>(M, invd, S, ld, kb, nb);
+      panel_u12<float, false>(M, S, ld, kb, nb);
+    }
+    tc_rect<4>(M, ld, kb, nb, kb + nb, S, kb + nb, S);
+    __syncthreads();
+  }
+  invert_upper_blocks<float>(M, invd, S, ld);
+}
+
 // LARGE: networks of 257..512 species (matrix in global memory): two panel
 // rows per thread and up to 16 column groups in the trailing update.
 template <typename LT, bool LARGE>
 __device__ void lu_blocked(LT* M, LT* invd, int S, int ld) {
+#if CBX_PAIR_PANELS && CBX_TC_LU
+  if constexpr (sizeof(LT) == 4 && LARGE) {
+    lu_blocked_pairs((float*)M, (float*)invd, S, ld);
+    return;
+  }
+#endif
   for (int kb = 0; kb < S; kb += NB) {
     const int nb = min(NB, S - kb);
     const bool two = LARGE && S - kb > NT;  // more panel rows than threads
