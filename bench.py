@@ -117,6 +117,13 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def network_counts(net):
+    """(two-body reactions, one-body reactions, stoichiometric entries) of a network."""
+    R_two = int(np.sum(net.rtype == synth.TWO_BODY))
+    n_nu = int(sum(np.sum(net.reac >= 0, axis=1)) + sum(np.sum(net.prod >= 0, axis=1)))
+    return R_two, net.n_reactions - R_two, n_nu
+
+
 def algorithmic_flops(info, st, R_two, R_one, n_nu):
     """FP64 (and FP32) flops of the method for the given per-cell counters.
 
@@ -327,9 +334,7 @@ def run_gpu(args):
     net = synth.make_network(S_SP, R_RX)
     N = carbox.Network.from_synth(net)
     info = N.info()
-    R_two = int(np.sum(net.rtype == synth.TWO_BODY))
-    R_one = net.n_reactions - R_two
-    n_nu = int(sum(np.sum(net.reac >= 0, axis=1)) + sum(np.sum(net.prod >= 0, axis=1)))
+    R_two, R_one, n_nu = network_counts(net)
     phi_h = shard_cells(synth.cells(CELLS * ws), rank, CELLS)
     x0_h = np.ascontiguousarray(np.repeat(synth.initial_abundances(net)[:, None], CELLS, axis=1))
     phi = torch.tensor(phi_h, device=dev)
@@ -412,7 +417,8 @@ def run_gpu(args):
     large = None
     if not args.no_large and ws == 1:
         with ClockSampler(local) as clk_l:
-            large = run_large_throughput(carbox, dev, stream, 4096, errors=rank == 0 and not args.no_cpu_baseline)
+            large = run_large_throughput(carbox, dev, stream, 4096, errors=rank == 0 and not args.no_cpu_baseline,
+                                         peaks=peaks)
         large["clocks"] = clk_l.summary()
 
     # ---- end to end through the host-buffer C-ABI call (copies inside the timed region)
@@ -523,14 +529,21 @@ def _gpu_setup():
     return torch, dev, carbox
 
 
-def run_large_throughput(carbox, dev, stream, cells, errors=True, n_err=4):
+def run_large_throughput(carbox, dev, stream, cells, errors=True, n_err=4, peaks=None):
     """500 species / 6000 reactions, 1 Myr: mixed and FP64 cell-solves/s on the same
-    `cells` seeded cells (one timed step each), and (errors) the per-species
+    `cells` seeded cells (one timed step each), each with its roofline (the
+    method's flops from the per-cell counters over the FMA peaks: `peaks` as
+    measured by measure_fma_peaks, else nominal), and (errors) the per-species
     relative error of both against the FP64 oracle on the first n_err cells
     (species above 1e-12), with element and charge conservation."""
     import torch
     net = synth.make_network(500, 6000)
     N = carbox.Network.from_synth(net)
+    info = N.info()
+    counts = network_counts(net)
+    fp64_peak = peaks["fp64_tflops"] if peaks else FP64_NOMINAL_TFLOPS
+    fp32_peak = peaks["fp32_tflops"] if peaks else FP32_NOMINAL_TFLOPS
+    peak_src = "measured in this run (FMA-chain probe)" if peaks else "nominal (probe not run)"
     phi_h = synth.cells(cells)
     x0_h = np.repeat(synth.initial_abundances(net)[:, None], cells, axis=1)
     phi = torch.tensor(phi_h, device=dev)
@@ -557,6 +570,26 @@ def run_large_throughput(carbox, dev, stream, cells, errors=True, n_err=4):
                      "cell_p99_ms": float(np.percentile(lat, 99)),
                      "steps_per_cell": float(sd["steps"].mean()), "lu_per_cell": float(sd["lu_factors"].mean()),
                      "refine_sweeps_per_newton": float(sd["refine_sweeps"].sum() / max(1, sd["newton_iters"].sum()))}
+        sec = ms / 1e3
+        if name == "fp64":
+            fl = algorithmic_flops(info, sd, *counts)
+            tot = float(sum(fl.values()))
+            out[name]["roofline"] = {"bound": "alu", "kernel": "solve_kernel<double, GM> (FP64 pipe)",
+                                     "achieved": tot / sec / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                                     "frac": tot / sec / 1e12 / fp64_peak, "flops_per_launch": tot,
+                                     "lu_share_of_flops": float(fl["lu"]) / tot, "peak_source": peak_src}
+        else:
+            f32, f64 = (float(v) for v in mixed_flops(info, sd, *counts))
+            out[name]["roofline"] = {"bound": "alu", "kernel": "solve_kernel<float, GM> (FP32 LU and solves, FP64 rest)",
+                                     "fp32": {"achieved": f32 / sec / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                                              "frac": f32 / sec / 1e12 / fp32_peak, "flops_per_launch": f32},
+                                     "fp64": {"achieved": f64 / sec / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                                              "frac": f64 / sec / 1e12 / fp64_peak, "flops_per_launch": f64},
+                                     "peak_source": peak_src}
+    # the roofline counts F_LU of the symbolic fill; the global-memory LU
+    # factors the whole matrix (lu_flops_dense per factorisation)
+    out["lu_fill"] = {"nnz_lu": int(info["nnz_lu"]), "dense_fraction": info["nnz_lu"] / 500.0 ** 2,
+                      "lu_flops": float(info["lu_flops"]), "lu_flops_dense": float(info["lu_flops_dense"])}
     out["mixed_speedup_vs_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
     if errors:
         ref = oracle_map(net, phi_h[:n_err], x0_h[:, 0], T_END)

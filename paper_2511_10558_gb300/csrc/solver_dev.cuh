@@ -554,16 +554,74 @@ __device__ void lu_crout64(const PivLists& P, double* M, double* invd) {
   __syncthreads();
 }
 
-// v <- D^{-1} L^{-1} v (L unit lower, D the pivots with reciprocals in invd),
-// blocks of 32: one warp solves the diagonal block with shuffles, then one
-// thread per row applies the block to the rows below (four partial sums to
-// shorten the FP64 dependency chain); D^{-1} last, element-wise.
-__device__ void forward_crout64(const double* M, const double* invd, int S, double* v) {
+// Triangular solves with the Crout factors, blocks of 32 with look-ahead.
+// Warp w runs on the SM sub-partition w % 4, and one warp issues at most one
+// FP64 instruction per ~67 cycles, so the 32-step chain of a diagonal block
+// (warp 0, shuffles) alone leaves most of the SM's FP64 pipe idle. While warp
+// 0 solves block b, the warps on the other three sub-partitions apply the
+// previous block to the rows beyond the next block (one thread per row, four
+// partial sums); after the barrier, warps 0..3 (one per sub-partition,
+// LA_COLS columns each) apply block b to the next block's rows alone, into
+// partial sums `part` [4][32] that warp 0 takes when it starts that block's
+// chain. Two barriers per block, as without look-ahead; the critical path per
+// block is the chain plus an eighth of the next block's update.
+constexpr int LA_COLS = 8;
+
+// bulk-update worker index of warp w (0..5 for the warps not on warp 0's
+// sub-partition), or -1
+__device__ __forceinline__ int la_worker(int w) { return (w & 3) == 0 ? -1 : (w >> 2) * 3 + (w & 3) - 1; }
+constexpr int LA_WORKERS = (NW / 4) * 3;
+
+// v[i] -= sum_{c < nc} row_i[c] y[c] for rows i in [i0, i1), one thread per
+// row of this worker
+__device__ __forceinline__ void la_bulk(const double* M, int ld, const double* y, int c0, int nc, double* v, int i0,
+                                        int i1, int wk, int lane) {
+  for (int i = i0 + 32 * wk + lane; i < i1; i += 32 * LA_WORKERS) {
+    const double* row = M + i * ld + c0;
+    double p0 = v[i], p1 = 0.0, p2 = 0.0, p3 = 0.0;
+    int c = 0;
+    for (; c + 4 <= nc; c += 4) {
+      p0 = fma(-row[c], y[c], p0);
+      p1 = fma(-row[c + 1], y[c + 1], p1);
+      p2 = fma(-row[c + 2], y[c + 2], p2);
+      p3 = fma(-row[c + 3], y[c + 3], p3);
+    }
+    for (; c < nc; ++c) p0 = fma(-row[c], y[c], p0);
+    v[i] = (p0 + p1) + (p2 + p3);
+  }
+}
+
+// part[32 w + lane] = sum of row (r0 + lane)'s entries in columns
+// c0 + LA_COLS w .. (below c0 + nc) times y; warps 0..3
+__device__ __forceinline__ void la_next(const double* M, int ld, const double* v, int c0, int nc, int r0, int r1,
+                                        double* part, int w, int lane) {
+  const int i = r0 + lane, cw = LA_COLS * w;
+  double p = 0.0, q = 0.0;
+  if (i < r1) {
+    const double* row = M + i * ld + c0 + cw;
+    const double* y = v + c0 + cw;
+#pragma unroll
+    for (int c = 0; c < LA_COLS; c += 2) {
+      if (cw + c < nc) p = fma(row[c], y[c], p);
+      if (cw + c + 1 < nc) q = fma(row[c + 1], y[c + 1], q);
+    }
+  }
+  part[32 * w + lane] = p + q;
+}
+
+// v <- D^{-1} L^{-1} v (L unit lower, D the pivots with reciprocals in invd);
+// D^{-1} last, element-wise. part: 128 doubles of shared scratch.
+__device__ void forward_crout64(const double* M, const double* invd, int S, double* v, double* part) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, ld = lead_dim(S);
-  for (int kb = 0; kb < S; kb += 32) {
-    const int nb = min(32, S - kb);
+  const int nblk = (S + 31) / 32, wk = la_worker(w);
+  for (int b = 0; b < nblk; ++b) {
+    const int kb = 32 * b, nb = min(32, S - kb);
     if (w == 0) {
-      double val = lane < nb ? v[kb + lane] : 0.0;
+      double val = 0.0;
+      if (lane < nb) {
+        val = v[kb + lane];
+        if (b > 0) val -= (part[lane] + part[32 + lane]) + (part[64 + lane] + part[96 + lane]);
+      }
       const double* row = M + (kb + min(lane, nb - 1)) * ld + kb;
 #pragma unroll
       for (int c = 0; c < 32; ++c) {
@@ -573,34 +631,32 @@ __device__ void forward_crout64(const double* M, const double* invd, int S, doub
         }
       }
       if (lane < nb) v[kb + lane] = val;
+    } else if (wk >= 0 && b > 0) {
+      // block b-1 (full) on the rows below block b (block b took it through
+      // the partial sums)
+      la_bulk(M, ld, v + kb - 32, kb - 32, 32, v, kb + 32, S, wk, lane);
     }
     __syncthreads();
-    for (int i = kb + nb + threadIdx.x; i < S; i += NT) {
-      const double* row = M + i * ld + kb;
-      double p0 = v[i], p1 = 0.0, p2 = 0.0, p3 = 0.0;
-      int c = 0;
-      for (; c + 4 <= nb; c += 4) {
-        p0 = fma(-row[c], v[kb + c], p0);
-        p1 = fma(-row[c + 1], v[kb + c + 1], p1);
-        p2 = fma(-row[c + 2], v[kb + c + 2], p2);
-        p3 = fma(-row[c + 3], v[kb + c + 3], p3);
-      }
-      for (; c < nb; ++c) p0 = fma(-row[c], v[kb + c], p0);
-      v[i] = (p0 + p1) + (p2 + p3);
-    }
+    if (b + 1 < nblk && w < 4) la_next(M, ld, v, kb, 32, kb + 32, S, part, w, lane);
     __syncthreads();
   }
   for (int i = threadIdx.x; i < S; i += NT) v[i] *= invd[i];
   __syncthreads();
 }
 
-// v <- U^{-1} v for the unit upper Crout factor, blocks of 32 from the bottom.
-__device__ void backward_crout64(const double* M, int S, double* v) {
+// v <- U^{-1} v for the unit upper Crout factor, blocks of 32 from the bottom
+// (the bottom block may be partial; the others are full).
+__device__ void backward_crout64(const double* M, int S, double* v, double* part) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, ld = lead_dim(S);
-  for (int kb = ((S - 1) / 32) * 32; kb >= 0; kb -= 32) {
-    const int nb = min(32, S - kb);
+  const int nblk = (S + 31) / 32, wk = la_worker(w);
+  for (int b = nblk - 1; b >= 0; --b) {
+    const int kb = 32 * b, nb = min(32, S - kb);
     if (w == 0) {
-      double val = lane < nb ? v[kb + lane] : 0.0;
+      double val = 0.0;
+      if (lane < nb) {
+        val = v[kb + lane];
+        if (b + 1 < nblk) val -= (part[lane] + part[32 + lane]) + (part[64 + lane] + part[96 + lane]);
+      }
       const double* row = M + (kb + min(lane, nb - 1)) * ld + kb;
 #pragma unroll
       for (int c = 31; c >= 0; --c) {
@@ -610,21 +666,14 @@ __device__ void backward_crout64(const double* M, int S, double* v) {
         }
       }
       if (lane < nb) v[kb + lane] = val;
+    } else if (wk >= 0 && b + 1 < nblk && b > 0) {
+      // block b+1 (possibly the partial bottom block) on the rows above block b
+      // (block b took it through the partial sums)
+      const int kn = kb + 32;
+      la_bulk(M, ld, v + kn, kn, min(32, S - kn), v, 0, kb, wk, lane);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kb; i += NT) {
-      const double* row = M + i * ld + kb;
-      double p0 = v[i], p1 = 0.0, p2 = 0.0, p3 = 0.0;
-      int c = 0;
-      for (; c + 4 <= nb; c += 4) {
-        p0 = fma(-row[c], v[kb + c], p0);
-        p1 = fma(-row[c + 1], v[kb + c + 1], p1);
-        p2 = fma(-row[c + 2], v[kb + c + 2], p2);
-        p3 = fma(-row[c + 3], v[kb + c + 3], p3);
-      }
-      for (; c < nb; ++c) p0 = fma(-row[c], v[kb + c], p0);
-      v[i] = (p0 + p1) + (p2 + p3);
-    }
+    if (b > 0 && w < 4) la_next(M, ld, v, kb, nb, kb - 32, kb, part, w, lane);
     __syncthreads();
   }
 }
@@ -1210,7 +1259,7 @@ __host__ __device__ inline size_t layout(int S, int R, int nseg, bool mixed, boo
   t.tmp = (double*)take(S * 8);
   t.r = (double*)take((size_t)R * 8);
   t.part = (double*)take((size_t)nseg * 8);
-  t.red = (double*)take(64 * 8);
+  t.red = (double*)take(128 * 8);  // block sums; the solves' look-ahead partials
   t.Tm = (double*)take(kMaxOrder * kMaxOrder * 8);
   t.v32 = (float*)take(mixed ? S * 4 : 0);
   t.pstage = (int*)take((size_t)piv_ints * 4);
@@ -1311,8 +1360,8 @@ __device__ void linear_solve(Cell<double, GM>& c, double cc, const double* w, do
   if constexpr (GM) {
     solve_blocked<double>(c.M, (const double*)c.s.invd, S, lead_dim(S), dy);
   } else {
-    forward_crout64(c.M, (const double*)c.s.invd, S, dy);
-    backward_crout64(c.M, S, dy);
+    forward_crout64(c.M, (const double*)c.s.invd, S, dy, c.s.red);
+    backward_crout64(c.M, S, dy, c.s.red);
   }
 }
 
