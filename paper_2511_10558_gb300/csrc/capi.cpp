@@ -84,6 +84,7 @@ int upload(cbx_network* n) {
   d.nnzJ = h.nnzJ;
   d.nseg = h.nseg;
   d.kdense = h.kdense;
+  d.sparse_panels = h.sparse_panels;
   d.rtype = (const int*)(b + o_rtype);
   d.alpha = (const double*)(b + o_alpha);
   d.beta = (const double*)(b + o_beta);

@@ -21,6 +21,7 @@ constexpr int kNumTypes = 4;           // CBX_TWO_BODY .. CBX_CR_PHOTO
 struct DevNet {
   int S, R, nnzJ, nseg;
   int kdense;            // pivots k >= kdense are factored over the full index ranges
+  int sparse_panels;     // leading 32-wide panels whose trailing update the FP64 blocked LU takes from the lists
   const int* rtype;      // [R]
   const double* alpha;   // [R]
   const double* beta;    // [R]
@@ -72,6 +73,7 @@ enum { kOpInit = 0, kOpRescale = 1, kOpStep = 2 };
 struct HostNet {
   int S = 0, R = 0, nnzJ = 0, nnzLU = 0, nseg = 0, kdense = 0;
   int head_ints = 0;  // 2 (kdense + 1) + entries of the sparse pivots' lists
+  int sparse_panels = 0;  // see DevNet
   double lu_flops = 0;
   std::vector<int> perm, iperm, rprod;
   std::vector<int> rtype, ra, rb;

@@ -273,6 +273,26 @@ std::string compile_network(const cbx_species* sp, int S, const cbx_reaction* rx
     }
   }
   n.head_ints = 2 * (n.kdense + 1) + n.piv_lptr[n.kdense] + n.piv_uptr[n.kdense];
+  // Leading 32-wide panels of the FP64 blocked LU (networks whose matrix lives
+  // in global memory) whose trailing update is applied from the pivot lists
+  // rather than as a dense rank-32 product: a panel counts while the
+  // structural work of its update, sum over its pivots of 2 |L(:,k)| |U(k,:)|
+  // restricted to the rows and columns after the panel, is below a quarter of
+  // the dense update's 2 * 32 * (S - panel end)^2 (a listed update costs a
+  // scattered read-modify-write per term, a dense one a register-tiled FMA).
+  n.sparse_panels = 0;
+  for (int kb = 0; kb + 32 < S; kb += 32) {
+    const int ke = kb + 32;
+    double work = 0.0;
+    for (int k = kb; k < ke; ++k) {
+      int nl = 0, nu = 0;
+      for (int e = n.piv_lptr[k]; e < n.piv_lptr[k + 1]; ++e) nl += n.piv_l[e] >= ke;
+      for (int e = n.piv_uptr[k]; e < n.piv_uptr[k + 1]; ++e) nu += n.piv_u[e] >= ke;
+      work += 2.0 * nl * nu;
+    }
+    if (work >= 0.25 * 2.0 * 32.0 * (double)(S - ke) * (S - ke)) break;
+    ++n.sparse_panels;
+  }
   n.lu_flops = flops;
   return "";
 }

@@ -1085,6 +1085,43 @@ __device__ void invert_upper_blocks(LT* M, const LT* invd, int S, int ld) {
   __syncthreads();
 }
 
+// A22 -= L21 U12 for one of the leading panels [kb, kb+NB) of a network whose
+// first pivots are sparse: one thread per trailing row i; for each pivot k of
+// the panel with L(i,k) != 0, the columns j >= kb+NB of U(k,:) from the
+// pivot's structural list (ascending). Rows are disjoint, so no two threads
+// write one element. Entries outside the pattern hold exact zeros, so the
+// skipped terms are exact zeros.
+template <typename LT>
+__device__ void sparse_panel_update(LT* M, int S, int ld, int kb, const int* uptr, const int* ucol) {
+  const int ke = kb + NB;
+  for (int i = ke + threadIdx.x; i < S; i += NT) {
+    LT* row = M + (size_t)i * ld;
+    for (int c = 0; c < NB; ++c) {
+      const LT l = row[kb + c];
+      if (l == LT(0)) continue;
+      const int k = kb + c;
+      const LT* urow = M + (size_t)k * ld;
+      const int e1 = uptr[k + 1];
+      int e = uptr[k];
+      while (e < e1 && ucol[e] < ke) ++e;  // columns inside the panel
+      for (; e + 4 <= e1; e += 4) {
+        const int j0 = ucol[e], j1 = ucol[e + 1], j2 = ucol[e + 2], j3 = ucol[e + 3];
+        const LT u0 = urow[j0], u1 = urow[j1], u2 = urow[j2], u3 = urow[j3];
+        const LT a0 = row[j0], a1 = row[j1], a2 = row[j2], a3 = row[j3];
+        row[j0] = a0 - l * u0;
+        row[j1] = a1 - l * u1;
+        row[j2] = a2 - l * u2;
+        row[j3] = a3 - l * u3;
+      }
+      for (; e < e1; ++e) {
+        const int j = ucol[e];
+        row[j] -= l * urow[j];
+      }
+    }
+  }
+  __syncthreads();
+}
+
 // FP32, matrix in global memory: panels in pairs, so that the trailing matrix
 // is read and written once per two panels (its passes are the DRAM traffic of
 // the factorisation). For panels P1 = [kb, k2) and P2 = [k2, ke): factor P1
@@ -1133,9 +1170,14 @@ __device__ __noinline__ void lu_blocked_pairs(float* M, float* invd, int S, int 
 }
 
 // LARGE: networks of 257..512 species (matrix in global memory): two panel
-// rows per thread and up to 16 column groups in the trailing update.
+// rows per thread and up to 16 column groups in the trailing update; in FP64
+// the first nsp panels take their trailing update from the pivots' U lists
+// (uptr, ucol). In FP32 the dense tensor-core update of those panels costs
+// less than the listed one: 500 species mixed measured 626 cell-solves/s
+// dense and 506 listed, FP64 194 dense and 220 listed.
 template <typename LT, bool LARGE>
-__device__ void lu_blocked(LT* M, LT* invd, int S, int ld) {
+__device__ void lu_blocked(LT* M, LT* invd, int S, int ld, int nsp = 0, const int* uptr = nullptr,
+                           const int* ucol = nullptr) {
 #if CBX_PAIR_PANELS && CBX_TC_LU
   if constexpr (sizeof(LT) == 4 && LARGE) {
     lu_blocked_pairs((float*)M, (float*)invd, S, ld);
@@ -1153,7 +1195,8 @@ __device__ void lu_blocked(LT* M, LT* invd, int S, int ld) {
       panel_factor<LT, false, 1>(M, invd, S, ld, kb, nb);
       panel_u12<LT, false>(M, S, ld, kb, nb);
     }
-    trailing_update<LT, LARGE>(M, S, ld, kb, nb);
+    if (LARGE && sizeof(LT) == 8 && kb < nsp * NB) sparse_panel_update<LT>(M, S, ld, kb, uptr, ucol);
+    else trailing_update<LT, LARGE>(M, S, ld, kb, nb);
   }
   invert_upper_blocks<LT>(M, invd, S, ld);
 }
@@ -1407,7 +1450,7 @@ template <typename LT, bool GM>
 __device__ void factor(Cell<LT, GM>& c, double cc) {
   build_matrix<LT>(c.n, c.Jv, cc, c.M);
   if constexpr (GM) {
-    lu_blocked<LT, true>(c.M, (LT*)c.s.invd, c.n.S, lead_dim(c.n.S));
+    lu_blocked<LT, true>(c.M, (LT*)c.s.invd, c.n.S, lead_dim(c.n.S), c.n.sparse_panels, c.n.piv_uptr, c.n.piv_u);
   } else {
     if constexpr (sizeof(LT) == 4)
       lu_blocked<LT, false>(c.M, (LT*)c.s.invd, c.n.S, lead_dim(c.n.S));
