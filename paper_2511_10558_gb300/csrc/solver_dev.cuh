@@ -262,11 +262,12 @@ __device__ void build_matrix(const DevNet& n, const double* Jv, double c, LT* M)
 // upper triangular, in place, without pivoting, on the static fill pattern.
 // Row k of U is stored pre-scaled by 1/pivot_k, so every warp applies the
 // rank-1 update a_ij -= a_ik u_kj (rows i of L(:,k), columns j of U(k,:)) with
-// no separate scaling phase: one barrier per pivot. Warp 0 updates row k+1
-// first and then prepares pivot k+1 (reciprocal pivot, row scaling) while the
-// other warps work on their rows. Pivots k >= kd are factored over the full
-// ranges k+1..S-1 (entries outside the pattern are exact zeros), without the
-// per-pivot index lists.
+// no separate scaling phase: one barrier per pivot in the sparse range. Warp 0
+// updates row k+1 first and then prepares pivot k+1 (reciprocal pivot, row
+// scaling) while the other warps work on their rows. Pivots k >= kd are
+// factored over the full ranges k+1..S-1 (entries outside the pattern are
+// exact zeros), without the per-pivot index lists, and there two pivots share
+// one barrier (dense_rank_rows).
 
 // Index lists of the sparse pivots k < kd (from the network tables, or a
 // copy of their head in shared memory).
